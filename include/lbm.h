@@ -1,0 +1,223 @@
+/*
+ * lbm.h -- C ABI of the GB300 two-component pseudo-potential lattice
+ * Boltzmann step (D3Q19) with the multiscale models of arXiv 2512.21696,
+ * "Enhanced numerical models for two-component fluid flow in multiscale
+ * porous structures".
+ *
+ * One time step (lbm_step) does, for every non-solid cell:
+ *   - pull streaming of both components with halfway bounce-back at solid
+ *     cells (LB equation, Eq. 2);
+ *   - moments: component densities rho^A, rho^B and momentum j;
+ *   - residual-component update in gray cells (Sec. II, Eq. 5, Fig. 6);
+ *   - forces: Shan-Chen inter-component force with psi = rho (Sec. II),
+ *     CSF surface-tension control (Eq. 4), the multiscale capillary and
+ *     viscous force of Eq. 1 with the tensorial resistivity of Eqs. 6-7,
+ *     and a constant body acceleration;
+ *   - collision projected on the second-order Hermite basis with the force
+ *     term of Eq. 3 (velocity u = (j + F/2)/rho; in gray cells u solves
+ *     (rho I + R/2) u = j + F_other/2 with the resistivity tensor R).
+ *
+ * Conventions
+ *   - Grids are nx*ny*nz cells, x fastest: cell (x,y,z) has linear index
+ *     x + nx*(y + ny*z).  Per-cell arrays are dense in that order; vector
+ *     fields are stored component-major, u[d*ncell + cell].
+ *   - Cell types: LBM_CELL_PORE (resolved fluid), LBM_CELL_SOLID,
+ *     LBM_CELL_GRAY (under-resolved porous cell with porosity 0 < phi < 1).
+ *   - Every call returns LBM_OK (0) or a negative LBM_ERR_* code and never
+ *     throws; lbm_strerror() turns a code into text.  After an error the
+ *     context stays valid unless the code is LBM_ERR_CUDA from a sticky CUDA
+ *     fault, in which case only lbm_destroy() may follow.
+ *   - Ownership: the context owns all device memory it allocates.  Array
+ *     arguments are read (or written) during the call only; the caller keeps
+ *     ownership.  `mem` says whether an array pointer is host memory
+ *     (LBM_MEM_HOST) or device memory of the context's device
+ *     (LBM_MEM_DEVICE, e.g. a torch tensor's data_ptr()).
+ *   - Streams: all device work is enqueued on lbm_params.stream (NULL = the
+ *     legacy default stream).  lbm_step and lbm_set_* calls are asynchronous
+ *     with respect to the host except that host-memory inputs are copied
+ *     before the call returns.  lbm_observables, lbm_get_fields (host output),
+ *     lbm_get_static and lbm_save_state synchronise the stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+#define LBM_MAX_PORE_TYPES 16
+
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,      /* invalid argument, size or ordering of calls */
+    LBM_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+    LBM_ERR_OOM = -3,      /* device or host allocation failed */
+    LBM_ERR_NUMERIC = -4,  /* non-finite or negative density detected */
+    LBM_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up */
+    LBM_ERR_STATE = -6     /* call out of order (e.g. step before geometry) */
+};
+
+enum lbm_mem { LBM_MEM_HOST = 0, LBM_MEM_DEVICE = 1 };
+
+enum lbm_cell { LBM_CELL_PORE = 0, LBM_CELL_SOLID = 1, LBM_CELL_GRAY = 2 };
+
+/* Population storage.  F32: the rest population f_0 and the deviations
+ * f_i - 3 w_i f_0 (i >= 1) of each cell, in FP32.  F16S / BF16S: the shifted
+ * deviations f_i - w_i rho0 (rho0 = (rho_hi + rho_lo)/2) in FP16 / BF16.
+ * All storages compute in FP32. */
+enum lbm_storage { LBM_STORAGE_F32 = 0, LBM_STORAGE_F16S = 1, LBM_STORAGE_BF16S = 2 };
+
+/* Model and run parameters.  Index 0 is component A, 1 is component B. */
+typedef struct lbm_params {
+    int nx, ny, nz;
+    int periodic[3];        /* 1: periodic axis; 0: the outside is solid wall */
+    double tau[2];          /* relaxation times; viscosity nu = (tau - 1/2)/3 */
+    double G;               /* Shan-Chen coupling: F^a = -G psi^a grad psi^other */
+    double kappa_csf;       /* Eq. 4 coefficient (negative lowers sigma) */
+    double phi_avg[2];      /* Eq. 4 characteristic average of phi^a */
+    double phi_max[2];      /* Eq. 4 characteristic maximum of phi^a */
+    int csf_everywhere;     /* 0: Eq. 4 only in gray cells; 1: in all cells */
+    double rho_wall[2];     /* virtual densities seen at solid cells (wetting) */
+    double body_accel[2][3];/* body acceleration per component; F = rho g */
+    int wet_idx;            /* index of the wetting component (water) */
+    double rho_hi, rho_lo;  /* bulk majority / minority densities */
+    double s_lo, s_hi;      /* residual hysteresis thresholds on s */
+    double at_cut;          /* H(At) = |grad At|/2 only where |At| <= at_cut */
+    double eps_n;           /* floor of |grad| in unit normals */
+    double kr_min;          /* floor of relative permeabilities */
+    double c_g;             /* weight of grad(phi) grad(phi)^T in the axis tensor */
+    int storage;            /* enum lbm_storage */
+    void *stream;           /* cudaStream_t for all work of this context */
+    double probe_center[3]; /* pressure probe for lbm_obs.dp */
+    double probe_r_in;      /* inside: distance < probe_r_in */
+    double probe_r_out;     /* outside: distance > probe_r_out */
+} lbm_params;
+
+/* Constitutive curves of one pore type (Appendix: Kozeny-Carman K0,
+ * capillary pressure and Corey relative permeabilities; Eq. 5 scaling).
+ *   K0(phi)  = kc_d^2 phi^3 / (180 (1 - phi)^2)
+ *   Pc(Sw)   = lamL(phi) pd Se^(-1/lambda),  Se = (Sw - swr)/(1 - swr) in [1e-2, 1]
+ *   lamL     = sqrt((K0(phi_ref)/phi_ref) / (K0(phi)/phi))        (Leverett)
+ *   Kr_w     = Se^nw,  Kr_n = (1 - Se)^nn                          (Se in [0, 1])
+ *   residual water Sw_irr = Sw at Pc = pc_ref_max_f * pd; residual oil
+ *   So_res = 1 - Sw at Pc = pc_ref_min_f * pd (Fig. 6 crossings)
+ *   aniso    = ratio a >= 1 of the principal permeabilities of Eq. 7:
+ *              K^D = diag(K0/a, K0, K0) along the principal axis e1. */
+typedef struct lbm_constitutive {
+    double kc_d, pd, lambda, swr, nw, nn, phi_ref, pc_ref_max_f, pc_ref_min_f, aniso;
+} lbm_constitutive;
+
+/* Observables of the current fields (FP64 reductions). */
+typedef struct lbm_obs {
+    double mass[2];      /* sum of rho^a over non-solid cells */
+    double sat;          /* sum(phi_c Sw)/sum(phi_c); phi_c = 1 pore, phi gray */
+    double flux_out;     /* mean u_x over the plane x = nx-1 (solid counts 0) */
+    double flux_vol[3];  /* mean of u over all cells (solid counts 0) */
+    double max_u;        /* max |u| over non-solid cells */
+    double dp;           /* mean p inside probe_r_in minus outside probe_r_out,
+                            p = (rhoA + rhoB)/3 + G rhoA rhoB */
+    long long nan_count; /* non-finite density or velocity values */
+    long long step;      /* steps taken since lbm_init_fields */
+} lbm_obs;
+
+/* Accumulated device time of one kernel, filled by lbm_profile_read. */
+typedef struct lbm_kernel_stat {
+    char name[32];
+    long long launches;
+    double total_ms;
+} lbm_kernel_stat;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Text of a status code (static storage). */
+const char *lbm_strerror(int code);
+
+/* LBM_ABI_VERSION of the loaded library. */
+int lbm_abi_version(void);
+
+/* Fill p with defaults for an nx*ny*nz periodic grid: tau = 1, G = 0,
+ * kappa_csf = 0, rho_hi/lo = 1/0.03, phi_avg = (rho_hi+rho_lo)/2,
+ * phi_max = rho_hi, rho_wall = (rho_hi+rho_lo)/2 (neutral wetting),
+ * wet_idx = 1, s_lo/s_hi = 0.1/0.9, at_cut = 0.95, eps_n = 1e-8 rho_hi,
+ * kr_min = 1e-6, c_g = 1, F32 storage, NULL stream, probe at the grid
+ * centre with r_in = 0, r_out = +inf.  LBM_ERR_ARG if p is NULL or a size
+ * is < 1. */
+int lbm_default_params(lbm_params *p, int nx, int ny, int nz);
+
+/* Fill c with the default curves: kc_d = 1, pd = 0.02, lambda = 2,
+ * swr = 0.15, nw = 3, nn = 2, phi_ref = 0.35, pc_ref_max_f = 3.5,
+ * pc_ref_min_f = 0.575 (midpoints of the ranges in Sec. II), aniso = 1. */
+int lbm_default_constitutive(lbm_constitutive *c);
+
+/* Create a context on the current CUDA device.  Validates p (sizes >= 1,
+ * tau > 1/2, rho_hi > rho_lo > 0 ... ; LBM_ERR_ARG otherwise) and allocates
+ * the population, density, field and geometry buffers (LBM_ERR_OOM if the
+ * device is too small).  *out is NULL on failure.  Every pore type starts
+ * with the default curves. */
+int lbm_create(lbm_ctx **out, const lbm_params *p);
+
+/* Free every device buffer and the handle.  NULL is accepted. */
+int lbm_destroy(lbm_ctx *ctx);
+
+/* Curves of pore type `pore_type` in [0, LBM_MAX_PORE_TYPES).  Takes effect
+ * at the next lbm_set_geometry.  LBM_ERR_ARG on an out-of-range type or
+ * invalid curve (pd <= 0, lambda <= 0, swr outside [0,1), aniso < 1, ...). */
+int lbm_set_constitutive(lbm_ctx *ctx, int pore_type, const lbm_constitutive *c);
+
+/* Geometry: type[ncell] (enum lbm_cell), phi[ncell] porosity of gray cells
+ * (values at pore/solid cells are ignored and taken as 1/0), pore_type[ncell]
+ * (may be NULL = all type 0).  Runs the FP64 geometry precompute on the
+ * device: gradient and Hessian of phi, principal axis of
+ * M = H H + c_g grad(phi) grad(phi)^T (Eqs. 6-7 and the abstract), K0,
+ * Leverett factor and residual amounts (Eq. 5, Fig. 6) of every gray cell.
+ * LBM_ERR_ARG on unknown cell codes or gray phi outside (0,1). */
+int lbm_set_geometry(lbm_ctx *ctx, const uint8_t *type, const float *phi,
+                     const uint8_t *pore_type, int mem);
+
+/* Equilibrium initial state of densities rhoA, rhoB [ncell] and velocity u
+ * [3][ncell] (NULL = at rest).  The residual flag of each cell starts wet
+ * when its normalised wetting density s >= 1/2, with no residual amount.
+ * Requires lbm_set_geometry first (LBM_ERR_STATE). */
+int lbm_init_fields(lbm_ctx *ctx, const float *rhoA, const float *rhoB, const float *u, int mem);
+
+/* Advance nsteps >= 0 time steps (asynchronous).  The fields read back by
+ * lbm_get_fields / lbm_observables are those of the last step. */
+int lbm_step(lbm_ctx *ctx, int nsteps);
+
+/* FP64 reductions of the current fields into *out (synchronises).
+ * Returns LBM_ERR_NUMERIC when nan_count > 0 (out is still filled). */
+int lbm_observables(lbm_ctx *ctx, lbm_obs *out);
+
+/* Current fields: rhoA, rhoB [ncell], u [3][ncell], sw [ncell] (effective
+ * water saturation incl. residual amounts); any pointer may be NULL.  Solid
+ * cells read 0. */
+int lbm_get_fields(lbm_ctx *ctx, float *rhoA, float *rhoB, float *u, float *sw, int mem);
+
+/* Geometry results of gray cells (zero elsewhere): kinv [6][ncell] = K^-1
+ * entries xx, yy, zz, xy, xz, yz (Eq. 7 inverse permeability, 1/length^2);
+ * pc_scale [ncell] = lamL(phi) pd; sw_irr, so_res [ncell]. */
+int lbm_get_static(lbm_ctx *ctx, float *kinv, float *pc_scale, float *sw_irr,
+                   float *so_res, int mem);
+
+/* Checkpoint of the populations, residual state and step counter. */
+int lbm_state_size(lbm_ctx *ctx, size_t *bytes);
+int lbm_save_state(lbm_ctx *ctx, void *host_buf, size_t bytes);
+int lbm_load_state(lbm_ctx *ctx, const void *host_buf, size_t bytes);
+
+/* Per-kernel CUDA-event timing of every launch while enabled (adds two
+ * event records per launch).  lbm_profile(ctx, 1) clears the counters.
+ * lbm_profile_read synchronises and writes up to max entries. */
+int lbm_profile(lbm_ctx *ctx, int enable);
+int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *count);
+
+/* Number of kernels the context has launched since creation. */
+int lbm_launch_count(lbm_ctx *ctx, long long *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
