@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Throughput of the two-component D3Q19 multiscale LB step on GB300.
+
+Workload: synthetic multiscale rock, 128^3 cells (20% solid Gaussian field,
+~19% gray cells with Kozeny-Carman/Brooks-Corey/Corey curves, CSF
+kappa = -0.045 in gray cells), component A driven from the x < 8 slab by a
+body force 1e-5 into the wetting component B.  One benchmark step is one full
+LB time step over the whole lattice (all kernels of the step).
+
+Prints one JSON line (rank 0).  Metric: MLUPS over all N^3 cells, whole job.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank advances its own replica (weak scaling); the
+timed region is bracketed by barriers and the slowest rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & HBM-roofline % of 2-comp D3Q19 step; mixed/adjoint/batched vs plain FP32"
+WORKLOAD = "drainage in synthetic multiscale rock, 128^3, 2-component D3Q19, FP32"
+EDGE = 128
+FALLBACK_HBM_GBS = 6800.0
+
+
+# --------------------------------------------------------------------- inputs
+def workload_inputs(edge=EDGE):
+    from paper_2512_21696_gb300 import synth
+    cell, phi, ptype = synth.drainage_geometry(edge, synth.SEED_BASE + 1)
+    rA, rB = synth.drainage_fields(cell, 1.0, 0.03)
+    return dict(cell=cell, phi=phi.astype(np.float32), ptype=ptype, rhoA=rA.astype(np.float32),
+                rhoB=rB.astype(np.float32))
+
+
+SETTINGS = dict(G=1.1, kappa_csf=-0.045, body_accel=((1e-5, 0.0, 0.0), (0.0, 0.0, 0.0)), rho_wall=(0.03, 1.0),
+                wet_idx=1)
+
+
+def algorithmic_bytes(cell):
+    """Bytes each kernel must move per launch (per-cell figures)."""
+    n = cell.size
+    fluid = int((cell != 1).sum())
+    gray = int((cell == 2).sum())
+    step = fluid * 304 + n * 1 + gray * 25
+    return dict(step=step,
+                k_collide=fluid * 304 + n * 1 + n * 8 + gray * 32,
+                k_density=fluid * 152 + n * 1 + n * 8), fluid, gray
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2512_21696_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_drainage128.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+source_sha:\s*(\w+)", text)
+    if not m or m.group(2) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.samples = []
+        self.proc = None
+        self.dev = device_index
+        self.window = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return None
+        t0, t1 = self.window or (0, float("inf"))
+        inwin = [p for (t, p) in self.samples if t0 - 0.15 <= t <= t1 + 0.15] or [p for _, p in self.samples]
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for p in inwin if num(p[1]) is not None]
+        mx = [num(p[2]) for p in inwin if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for p in inwin for k in range(4) if p[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(inwin)}
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2512_21696_gb300 import lbm
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    inp = workload_inputs()
+    cell = inp["cell"]
+    nz, ny, nx = cell.shape
+    n = cell.size
+    stream = torch.cuda.current_stream()
+    p = lbm.lbm_default_params(nx, ny, nz, stream=stream.cuda_stream, **SETTINGS)
+    ctx = lbm.lbm_create(p)
+    lbm.lbm_set_constitutive(ctx, 0, lbm.lbm_default_constitutive())
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in inp.items()}
+    lbm.lbm_set_geometry(ctx, dev["cell"], dev["phi"], dev["ptype"])
+    lbm.lbm_init_fields(ctx, dev["rhoA"], dev["rhoB"])
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    for _ in range(args.warmup):
+        lbm.lbm_step(ctx, 1)
+    torch.cuda.synchronize()
+
+    launches0 = lbm.lbm_launch_count(ctx)
+    lbm.lbm_profile(ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        lbm.lbm_step(ctx, 1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if dist:
+        dist.barrier()
+    clocks.mark(t_wall0, t_wall1)
+    ms = ev0.elapsed_time(ev1)
+    prof = lbm.lbm_profile_read(ctx)
+    lbm.lbm_profile(ctx, False)
+    launches = lbm.lbm_launch_count(ctx) - launches0
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    obs = lbm.lbm_observables(ctx, check=False)
+
+    # end-to-end through the public API with pinned host buffers
+    host = {k: torch.from_numpy(np.ascontiguousarray(inp[k])).pin_memory() for k in ("rhoA", "rhoB")}
+    outs = [torch.empty(s, dtype=torch.float32).pin_memory() for s in ((nz, ny, nx), (nz, ny, nx), (3, nz, ny, nx),
+                                                                       (nz, ny, nx))]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    lbm.lbm_init_fields(ctx, host["rhoA"].numpy(), host["rhoB"].numpy())
+    lbm.lbm_step(ctx, args.steps)
+    lbm.lbm_get_fields(ctx, *[o.numpy() for o in outs])
+    obs_e2e = lbm.lbm_observables(ctx, check=False)
+    e_ms = (time.perf_counter() - e0) * 1e3
+    if dist:
+        t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
+    clocks.stop()
+    ctx.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    alg, fluid, gray = algorithmic_bytes(cell)
+    mlups = world * n * args.steps / (ms * 1e-3) / 1e6
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("k_collide", (args.steps, ms))
+    dname, (dlaunch, dtotal) = dom
+    avg_s = dtotal / max(dlaunch, 1) * 1e-3
+    peak, peak_kind = measured_peak()
+    achieved = alg.get(dname, alg["step"]) / avg_s / 1e9
+    step_gbs = alg["step"] * args.steps / (ms * 1e-3) / 1e9
+    h2d = 2 * n * 4
+    d2h = 6 * n * 4 + 128
+    out = {
+        "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded multiscale-rock recipe)",
+        "config": {"workload": WORKLOAD, "cells": n, "fluid_frac": round(fluid / n, 4),
+                   "gray_frac": round(gray / n, 4), "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (2 x 319 MB population buffers)",
+                   "kernels_per_step": round(launches / args.steps, 3)},
+        "roofline": {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
+                     "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": ncu_traffic(dname),
+                     "alg_bytes_per_launch": alg.get(dname, alg["step"]),
+                     "avg_launch_ms": round(avg_s * 1e3, 5)},
+        "step_roofline": {"alg_bytes_per_cell": round(alg["step"] / n, 2), "achieved_gbs": round(step_gbs, 1),
+                          "frac": round(step_gbs / peak, 4)},
+        "kernels": {k: {"launches": v[0], "avg_ms": round(v[1] / max(v[0], 1), 5)} for k, v in prof.items()},
+        "e2e": {"value": round(world * n * args.steps / (e_ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "ms_total": round(e_ms, 3)},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(),
+        "observables": {"mass": obs["mass"], "sat": obs["sat"], "nan_count": obs["nan_count"],
+                        "e2e_nan_count": obs_e2e["nan_count"]},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(inp, budget_s=args.cpu_budget)
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ oracle timing
+def _oracle_slab(inp, nzs):
+    """Oracle on the first nzs z-planes of the workload (a bounded sample)."""
+    import oracle as O
+    from paper_2512_21696_gb300 import synth
+    cell = np.ascontiguousarray(inp["cell"][:nzs])
+    shape = cell.shape
+    p = O.make_params(shape, G=SETTINGS["G"], kappa=SETTINGS["kappa_csf"], accel=SETTINGS["body_accel"],
+                      rho_wall=SETTINGS["rho_wall"], wet=SETTINGS["wet_idx"])
+    o = O.Oracle(p, cell, inp["phi"][:nzs].astype(np.float64), ptype=inp["ptype"][:nzs], curves=[O.make_curve()])
+    o.init_fields(inp["rhoA"][:nzs].astype(np.float64), inp["rhoB"][:nzs].astype(np.float64))
+    return o, int(np.prod(shape))
+
+
+def cpu_baseline(inp, budget_s=15.0):
+    import oracle as O
+    O.build()
+    o, cells = _oracle_slab(inp, inp["cell"].shape[0])
+    t = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t
+    k = max(1, int(budget_s / max(one, 1e-3)))
+    t = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t
+    return {"value": round(cells * k / dt / 1e6, 3), "unit": "MLUPS", "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"full 128^3 workload, {k} timed FP64 steps after 1 untimed ({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    inp = workload_inputs()
+    nz = inp["cell"].shape[0]
+    budget = 150.0 / max(args.steps + args.warmup, 1)
+    probe, _ = _oracle_slab(inp, 8)
+    t = time.perf_counter()
+    probe.step(1)
+    per_plane = (time.perf_counter() - t) / 8
+    nzs = int(min(nz, max(1, budget / max(per_plane, 1e-6))))
+    o, cells = _oracle_slab(inp, nzs)
+    o.step(args.warmup)
+    t = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t
+    mlups = cells * args.steps / dt / 1e6
+    sample = f"first {nzs} of {nz} z-planes of the 128^3 workload per step"
+    out = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded multiscale-rock recipe)",
+           "config": {"workload": WORKLOAD, "cells": cells, "sample": sample},
+           "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": O.max_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

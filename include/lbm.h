@@ -48,6 +48,12 @@
 extern "C" {
 #endif
 
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
 #define LBM_ABI_VERSION 1
 #define LBM_MAX_PORE_TYPES 16
 
@@ -134,10 +140,18 @@ typedef struct lbm_kernel_stat {
 typedef struct lbm_ctx lbm_ctx;
 
 /* Text of a status code (static storage). */
-const char *lbm_strerror(int code);
+LBM_API const char *lbm_strerror(int code);
+
+/* Text of the last CUDA runtime error seen by the library in the calling
+ * thread ("" if none); valid until the next failing call in that thread. */
+LBM_API const char *lbm_last_cuda_error(void);
+
+/* sizeof of the ABI structures, for binding layout checks: which = 0
+ * lbm_params, 1 lbm_constitutive, 2 lbm_obs, 3 lbm_kernel_stat; 0 otherwise. */
+LBM_API size_t lbm_struct_size(int which);
 
 /* LBM_ABI_VERSION of the loaded library. */
-int lbm_abi_version(void);
+LBM_API int lbm_abi_version(void);
 
 /* Fill p with defaults for an nx*ny*nz periodic grid: tau = 1, G = 0,
  * kappa_csf = 0, rho_hi/lo = 1/0.03, phi_avg = (rho_hi+rho_lo)/2,
@@ -146,27 +160,27 @@ int lbm_abi_version(void);
  * kr_min = 1e-6, c_g = 1, F32 storage, NULL stream, probe at the grid
  * centre with r_in = 0, r_out = +inf.  LBM_ERR_ARG if p is NULL or a size
  * is < 1. */
-int lbm_default_params(lbm_params *p, int nx, int ny, int nz);
+LBM_API int lbm_default_params(lbm_params *p, int nx, int ny, int nz);
 
 /* Fill c with the default curves: kc_d = 1, pd = 0.02, lambda = 2,
  * swr = 0.15, nw = 3, nn = 2, phi_ref = 0.35, pc_ref_max_f = 3.5,
  * pc_ref_min_f = 0.575 (midpoints of the ranges in Sec. II), aniso = 1. */
-int lbm_default_constitutive(lbm_constitutive *c);
+LBM_API int lbm_default_constitutive(lbm_constitutive *c);
 
 /* Create a context on the current CUDA device.  Validates p (sizes >= 1,
  * tau > 1/2, rho_hi > rho_lo > 0 ... ; LBM_ERR_ARG otherwise) and allocates
  * the population, density, field and geometry buffers (LBM_ERR_OOM if the
  * device is too small).  *out is NULL on failure.  Every pore type starts
  * with the default curves. */
-int lbm_create(lbm_ctx **out, const lbm_params *p);
+LBM_API int lbm_create(lbm_ctx **out, const lbm_params *p);
 
 /* Free every device buffer and the handle.  NULL is accepted. */
-int lbm_destroy(lbm_ctx *ctx);
+LBM_API int lbm_destroy(lbm_ctx *ctx);
 
 /* Curves of pore type `pore_type` in [0, LBM_MAX_PORE_TYPES).  Takes effect
  * at the next lbm_set_geometry.  LBM_ERR_ARG on an out-of-range type or
  * invalid curve (pd <= 0, lambda <= 0, swr outside [0,1), aniso < 1, ...). */
-int lbm_set_constitutive(lbm_ctx *ctx, int pore_type, const lbm_constitutive *c);
+LBM_API int lbm_set_constitutive(lbm_ctx *ctx, int pore_type, const lbm_constitutive *c);
 
 /* Geometry: type[ncell] (enum lbm_cell), phi[ncell] porosity of gray cells
  * (values at pore/solid cells are ignored and taken as 1/0), pore_type[ncell]
@@ -175,47 +189,47 @@ int lbm_set_constitutive(lbm_ctx *ctx, int pore_type, const lbm_constitutive *c)
  * M = H H + c_g grad(phi) grad(phi)^T (Eqs. 6-7 and the abstract), K0,
  * Leverett factor and residual amounts (Eq. 5, Fig. 6) of every gray cell.
  * LBM_ERR_ARG on unknown cell codes or gray phi outside (0,1). */
-int lbm_set_geometry(lbm_ctx *ctx, const uint8_t *type, const float *phi,
+LBM_API int lbm_set_geometry(lbm_ctx *ctx, const uint8_t *type, const float *phi,
                      const uint8_t *pore_type, int mem);
 
 /* Equilibrium initial state of densities rhoA, rhoB [ncell] and velocity u
  * [3][ncell] (NULL = at rest).  The residual flag of each cell starts wet
  * when its normalised wetting density s >= 1/2, with no residual amount.
  * Requires lbm_set_geometry first (LBM_ERR_STATE). */
-int lbm_init_fields(lbm_ctx *ctx, const float *rhoA, const float *rhoB, const float *u, int mem);
+LBM_API int lbm_init_fields(lbm_ctx *ctx, const float *rhoA, const float *rhoB, const float *u, int mem);
 
 /* Advance nsteps >= 0 time steps (asynchronous).  The fields read back by
  * lbm_get_fields / lbm_observables are those of the last step. */
-int lbm_step(lbm_ctx *ctx, int nsteps);
+LBM_API int lbm_step(lbm_ctx *ctx, int nsteps);
 
 /* FP64 reductions of the current fields into *out (synchronises).
  * Returns LBM_ERR_NUMERIC when nan_count > 0 (out is still filled). */
-int lbm_observables(lbm_ctx *ctx, lbm_obs *out);
+LBM_API int lbm_observables(lbm_ctx *ctx, lbm_obs *out);
 
 /* Current fields: rhoA, rhoB [ncell], u [3][ncell], sw [ncell] (effective
  * water saturation incl. residual amounts); any pointer may be NULL.  Solid
  * cells read 0. */
-int lbm_get_fields(lbm_ctx *ctx, float *rhoA, float *rhoB, float *u, float *sw, int mem);
+LBM_API int lbm_get_fields(lbm_ctx *ctx, float *rhoA, float *rhoB, float *u, float *sw, int mem);
 
 /* Geometry results of gray cells (zero elsewhere): kinv [6][ncell] = K^-1
  * entries xx, yy, zz, xy, xz, yz (Eq. 7 inverse permeability, 1/length^2);
  * pc_scale [ncell] = lamL(phi) pd; sw_irr, so_res [ncell]. */
-int lbm_get_static(lbm_ctx *ctx, float *kinv, float *pc_scale, float *sw_irr,
+LBM_API int lbm_get_static(lbm_ctx *ctx, float *kinv, float *pc_scale, float *sw_irr,
                    float *so_res, int mem);
 
 /* Checkpoint of the populations, residual state and step counter. */
-int lbm_state_size(lbm_ctx *ctx, size_t *bytes);
-int lbm_save_state(lbm_ctx *ctx, void *host_buf, size_t bytes);
-int lbm_load_state(lbm_ctx *ctx, const void *host_buf, size_t bytes);
+LBM_API int lbm_state_size(lbm_ctx *ctx, size_t *bytes);
+LBM_API int lbm_save_state(lbm_ctx *ctx, void *host_buf, size_t bytes);
+LBM_API int lbm_load_state(lbm_ctx *ctx, const void *host_buf, size_t bytes);
 
 /* Per-kernel CUDA-event timing of every launch while enabled (adds two
  * event records per launch).  lbm_profile(ctx, 1) clears the counters.
  * lbm_profile_read synchronises and writes up to max entries. */
-int lbm_profile(lbm_ctx *ctx, int enable);
-int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *count);
+LBM_API int lbm_profile(lbm_ctx *ctx, int enable);
+LBM_API int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *count);
 
 /* Number of kernels the context has launched since creation. */
-int lbm_launch_count(lbm_ctx *ctx, long long *count);
+LBM_API int lbm_launch_count(lbm_ctx *ctx, long long *count);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,59 @@
+// Host-side context of one lattice and the internal launch interface between
+// the C-ABI layer (lbm_api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "lbm_common.cuh"
+
+struct lbm_ctx {
+    lbm_params p;
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    int n = 0;
+    lbm::DevParams dp{};
+    lbm_constitutive curves[LBM_MAX_PORE_TYPES];
+
+    // device buffers (owned)
+    float *f[2] = {nullptr, nullptr};  // populations [2][19][n], ping-pong
+    int cur = 0;                       // buffer holding the latest state
+    uint8_t *type = nullptr;           // [n]
+    float *phi = nullptr;              // [n] porosity (1 pore, 0 solid)
+    lbm::GrayRec *gray = nullptr;      // [n], valid at gray cells only
+    float *rho = nullptr;              // [2][n] densities of the current step
+    float *macro = nullptr;            // [6][n] rhoA, rhoB, ux, uy, uz, Sw
+    double *red = nullptr;             // reduction partials
+    int red_blocks = 0;
+
+    bool has_geometry = false;
+    bool has_fields = false;
+    long long steps = 0;
+    long long launches = 0;
+
+    struct ProfRec {
+        const char *name;
+        cudaEvent_t a, b;
+    };
+    bool profiling = false;
+    std::vector<ProfRec> prof;
+};
+
+namespace lbm {
+
+// Kernel launches (each records itself in ctx->launches and, while profiling,
+// brackets the launch with CUDA events).
+cudaError_t launch_init(lbm_ctx *ctx, const float *rhoA, const float *rhoB, const float *u);
+cudaError_t launch_density(lbm_ctx *ctx);
+cudaError_t launch_collide(lbm_ctx *ctx, bool write_macro);
+cudaError_t launch_geometry(lbm_ctx *ctx, const uint8_t *ptype);
+cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16);
+cudaError_t launch_static_out(lbm_ctx *ctx, float *kinv6, float *pcs, float *swirr, float *sores);
+
+// Profiling helpers used around launches.
+void prof_begin(lbm_ctx *ctx, const char *name, cudaEvent_t *ev_out);
+void prof_end(lbm_ctx *ctx, const char *name, cudaEvent_t ev_begin);
+
+}  // namespace lbm

@@ -1,0 +1,158 @@
+// Geometry precompute of the gray cells, in FP64 on the device (runs once
+// per lbm_set_geometry).
+//
+// Per gray cell (Eqs. 5-7 and the abstract's "Hessian and gradient of the
+// local porosity"):
+//   grad(phi)  isotropic D3Q19 stencil (1/cs^2) sum_i w_i phi(x+c_i) c_i;
+//   Hessian    second differences along the axes, four-point cross terms;
+//   M = H H + c_g grad(phi) grad(phi)^T; its top eigenvector e1 is the axis
+//   of lowest permeability, K = B diag(K0/a, K0, K0) B^T, so
+//   K^-1 = (1/K0)(I + (a-1) e1 e1^T); ties (mu1 - mu2 <= 1e-12 mu1) fall back
+//   to isotropic;
+//   K0 (Kozeny-Carman), Leverett factor lamL (Eq. 5), and the residual
+//   amounts from the crossings of Pc(Sw; phi) with pc_ref_max_f*pd and
+//   pc_ref_min_f*pd (Fig. 6).
+// The eigenvalues come from the closed-form trigonometric solution of the
+// characteristic cubic (Smith, 1961) and e1 from the largest cross product of
+// two rows of M - mu1 I.
+#include <cmath>
+
+#include "lbm_context.h"
+
+namespace lbm {
+
+struct CurveTable {
+    lbm_constitutive c[MAX_TYPES];
+};
+
+__device__ __forceinline__ double phi_of(const uint8_t *__restrict__ type, const float *__restrict__ phi,
+                                         int m)
+{
+    if (m < 0) return 0.0;
+    const uint8_t t = type[m];
+    return t == CELL_PORE ? 1.0 : (t == CELL_SOLID ? 0.0 : (double)phi[m]);
+}
+
+__device__ __forceinline__ int nbr(const DevParams &P, int x, int y, int z, int dx, int dy, int dz)
+{
+    const int X = axis_nb(x, dx, P.nx, P.per[0]);
+    const int Y = axis_nb(y, dy, P.ny, P.per[1]);
+    const int Z = axis_nb(z, dz, P.nz, P.per[2]);
+    return (X < 0 || Y < 0 || Z < 0) ? -1 : X + P.nx * (Y + P.ny * Z);
+}
+
+__device__ __forceinline__ double kozeny(const lbm_constitutive &cv, double phi)
+{
+    return cv.kc_d * cv.kc_d * phi * phi * phi / (180.0 * (1.0 - phi) * (1.0 - phi));
+}
+
+// Top eigenvector of a symmetric 3x3 matrix; returns false on a tie.
+__device__ bool top_eigvec(const double M[3][3], double e[3])
+{
+    const double p1 = M[0][1] * M[0][1] + M[0][2] * M[0][2] + M[1][2] * M[1][2];
+    const double q = (M[0][0] + M[1][1] + M[2][2]) / 3.0;
+    const double d0 = M[0][0] - q, d1 = M[1][1] - q, d2 = M[2][2] - q;
+    const double p2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * p1;
+    const double p = sqrt(p2 / 6.0);
+    if (!(p > 0.0)) return false;
+    const double B00 = d0 / p, B11 = d1 / p, B22 = d2 / p;
+    const double B01 = M[0][1] / p, B02 = M[0][2] / p, B12 = M[1][2] / p;
+    const double det = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) +
+                       B02 * (B01 * B12 - B11 * B02);
+    double r = 0.5 * det;
+    r = r < -1.0 ? -1.0 : (r > 1.0 ? 1.0 : r);
+    const double ang = acos(r) / 3.0;
+    const double mu1 = q + 2.0 * p * cos(ang);
+    const double mu3 = q + 2.0 * p * cos(ang + 2.0943951023931954923);  // + 2 pi/3
+    const double mu2 = 3.0 * q - mu1 - mu3;
+    if (mu1 - mu2 <= 1e-12 * fmax(mu1, 1e-30)) return false;
+    const double R[3][3] = {{M[0][0] - mu1, M[0][1], M[0][2]},
+                            {M[1][0], M[1][1] - mu1, M[1][2]},
+                            {M[2][0], M[2][1], M[2][2] - mu1}};
+    double best[3] = {0, 0, 0}, bn = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b) {
+            const double cr[3] = {R[a][1] * R[b][2] - R[a][2] * R[b][1],
+                                  R[a][2] * R[b][0] - R[a][0] * R[b][2],
+                                  R[a][0] * R[b][1] - R[a][1] * R[b][0]};
+            const double nn = cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2];
+            if (nn > bn) {
+                bn = nn;
+                best[0] = cr[0]; best[1] = cr[1]; best[2] = cr[2];
+            }
+        }
+    if (!(bn > 0.0)) return false;
+    const double inv = 1.0 / sqrt(bn);
+    for (int d = 0; d < 3; ++d) e[d] = best[d] * inv;
+    return true;
+}
+
+__global__ void k_geometry(DevParams P, CurveTable T, double c_g, const uint8_t *__restrict__ type,
+                           const float *__restrict__ phi, const uint8_t *__restrict__ ptype,
+                           GrayRec *__restrict__ gray)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P.n) return;
+    if (type[c] != CELL_GRAY) return;
+    const int x = c % P.nx, y = (c / P.nx) % P.ny, z = c / (P.nx * P.ny);
+    const double ph = (double)phi[c];
+    double g[3] = {0.0, 0.0, 0.0};
+    for (int i = 1; i < Q; ++i) {
+        const double v = phi_of(type, phi, nbr(P, x, y, z, cx(i), cy(i), cz(i)));
+        g[0] += 3.0 * wgt_d(i) * cx(i) * v;
+        g[1] += 3.0 * wgt_d(i) * cy(i) * v;
+        g[2] += 3.0 * wgt_d(i) * cz(i) * v;
+    }
+    double H[3][3];
+    for (int a = 0; a < 3; ++a) {
+        int ea[3] = {0, 0, 0};
+        ea[a] = 1;
+        H[a][a] = phi_of(type, phi, nbr(P, x, y, z, ea[0], ea[1], ea[2])) - 2.0 * ph +
+                  phi_of(type, phi, nbr(P, x, y, z, -ea[0], -ea[1], -ea[2]));
+        for (int b = a + 1; b < 3; ++b) {
+            int eb[3] = {0, 0, 0};
+            eb[b] = 1;
+            const double pp = phi_of(type, phi, nbr(P, x, y, z, ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2]));
+            const double pm = phi_of(type, phi, nbr(P, x, y, z, ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2]));
+            const double mp = phi_of(type, phi, nbr(P, x, y, z, eb[0] - ea[0], eb[1] - ea[1], eb[2] - ea[2]));
+            const double mm = phi_of(type, phi, nbr(P, x, y, z, -ea[0] - eb[0], -ea[1] - eb[1], -ea[2] - eb[2]));
+            H[a][b] = H[b][a] = 0.25 * (pp - pm - mp + mm);
+        }
+    }
+    double M[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            M[a][b] = H[a][0] * H[0][b] + H[a][1] * H[1][b] + H[a][2] * H[2][b] + c_g * g[a] * g[b];
+    const int pt = ptype ? (int)ptype[c] : 0;
+    const lbm_constitutive cv = T.c[pt];
+    double e[3] = {0.0, 0.0, 0.0};
+    const bool axis = top_eigvec(M, e);
+    const double sa = axis ? sqrt(cv.aniso - 1.0) : 0.0;
+    const double K0 = kozeny(cv, ph);
+    const double kref = kozeny(cv, cv.phi_ref);
+    const double lamL = sqrt((kref / cv.phi_ref) / (K0 / ph));
+    const double se_max = fmin(pow(cv.pc_ref_max_f / lamL, -cv.lambda), 1.0);
+    const double se_min = fmin(pow(cv.pc_ref_min_f / lamL, -cv.lambda), 1.0);
+    const double sw_irr = cv.swr + (1.0 - cv.swr) * se_max;
+    const double so_res = 1.0 - (cv.swr + (1.0 - cv.swr) * se_min);
+    GrayRec rec;
+    rec.a = make_float4((float)(sa * e[0]), (float)(sa * e[1]), (float)(sa * e[2]), (float)(1.0 / K0));
+    rec.b = make_float4((float)(lamL * cv.pd), (float)sw_irr, (float)so_res,
+                        __uint_as_float((unsigned)pt & 0xffu));
+    gray[c] = rec;
+}
+
+cudaError_t launch_geometry(lbm_ctx *ctx, const uint8_t *ptype)
+{
+    CurveTable T;
+    for (int k = 0; k < MAX_TYPES; ++k) T.c[k] = ctx->curves[k];
+    cudaEvent_t e0;
+    prof_begin(ctx, "k_geometry", &e0);
+    k_geometry<<<(ctx->n + 127) / 128, 128, 0, ctx->stream>>>(ctx->dp, T, ctx->p.c_g, ctx->type, ctx->phi,
+                                                               ptype, ctx->gray);
+    prof_end(ctx, "k_geometry", e0);
+    ctx->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

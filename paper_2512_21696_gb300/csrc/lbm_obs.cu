@@ -1,0 +1,192 @@
+// Observables of the current fields (FP64 reductions) and read-back of the
+// gray-cell geometry results.
+//
+// k_obs_partial: grid-stride pass, per-thread FP64 accumulators, warp-shuffle
+//                and shared-memory block reduction, one row of partials per
+//                block in the reduction scratch;
+// k_obs_final:   one block sums the rows in a fixed order (deterministic).
+#include <cfloat>
+
+#include "lbm_context.h"
+
+namespace lbm {
+
+constexpr int NOBS = 16;
+// slots: 0,1 mass; 2 sum phi_c Sw; 3 sum phi_c; 4 outlet u_x; 5..7 sum u;
+//        8 max |u|; 9 sum p inside; 10 count inside; 11 sum p outside;
+//        12 count outside; 13 non-finite count
+constexpr int SLOT_MAX = 8;
+constexpr int OBS_BLOCK = 256;
+constexpr int OBS_MAX_BLOCKS = 1024;
+
+struct ObsArgs {
+    double cx, cy, cz, rin2, rout2, G;
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Reduce acc[NOBS] over the block; thread 0 gets the result.
+__device__ void block_reduce(double acc[NOBS], double *sh /* [NOBS][32] */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NOBS; ++k) {
+        double v = (k == SLOT_MAX) ? warp_max(acc[k]) : warp_sum(acc[k]);
+        if (lane == 0) sh[k * 32 + warp] = v;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NOBS; ++k) {
+            double v = lane < nw ? sh[k * 32 + lane] : (k == SLOT_MAX ? 0.0 : 0.0);
+            v = (k == SLOT_MAX) ? warp_max(v) : warp_sum(v);
+            acc[k] = v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs O,
+                                                           const uint8_t *__restrict__ type,
+                                                           const float *__restrict__ phi,
+                                                           const float *__restrict__ macro,
+                                                           double *__restrict__ partial)
+{
+    __shared__ double sh[NOBS * 32];
+    double acc[NOBS];
+#pragma unroll
+    for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
+    const int n = P.n;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const uint8_t t = type[c];
+        if (t == CELL_SOLID) continue;
+        const double ra = macro[c], rb = macro[(size_t)n + c];
+        const double u0 = macro[(size_t)2 * n + c], u1 = macro[(size_t)3 * n + c], u2 = macro[(size_t)4 * n + c];
+        const double sw = macro[(size_t)5 * n + c];
+        if (!isfinite(ra) || !isfinite(rb) || !isfinite(u0) || !isfinite(u1) || !isfinite(u2)) {
+            acc[13] += 1.0;
+            continue;
+        }
+        const int x = c % P.nx, y = (c / P.nx) % P.ny, z = c / (P.nx * P.ny);
+        acc[0] += ra;
+        acc[1] += rb;
+        const double phc = t == CELL_GRAY ? (double)phi[c] : 1.0;
+        acc[2] += phc * sw;
+        acc[3] += phc;
+        if (x == P.nx - 1) acc[4] += u0;
+        acc[5] += u0;
+        acc[6] += u1;
+        acc[7] += u2;
+        acc[8] = fmax(acc[8], sqrt(u0 * u0 + u1 * u1 + u2 * u2));
+        const double dx = x - O.cx, dy = y - O.cy, dz = z - O.cz;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        const double pr = (ra + rb) / 3.0 + O.G * ra * rb;
+        if (r2 < O.rin2) { acc[9] += pr; acc[10] += 1.0; }
+        if (r2 > O.rout2) { acc[11] += pr; acc[12] += 1.0; }
+    }
+    block_reduce(acc, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NOBS; ++k) partial[(size_t)blockIdx.x * NOBS + k] = acc[k];
+}
+
+__global__ void __launch_bounds__(OBS_BLOCK) k_obs_final(const double *__restrict__ partial, int nblocks,
+                                                         double *__restrict__ out)
+{
+    __shared__ double sh[NOBS * 32];
+    double acc[NOBS];
+#pragma unroll
+    for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NOBS; ++k) {
+            const double v = partial[(size_t)b * NOBS + k];
+            acc[k] = (k == SLOT_MAX) ? fmax(acc[k], v) : acc[k] + v;
+        }
+    block_reduce(acc, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NOBS; ++k) out[k] = acc[k];
+}
+
+int obs_blocks(int n)
+{
+    int b = (n + OBS_BLOCK - 1) / OBS_BLOCK;
+    return b < OBS_MAX_BLOCKS ? (b < 1 ? 1 : b) : OBS_MAX_BLOCKS;
+}
+
+// Fills host_out16 (synchronises the stream).  red must hold
+// (obs_blocks(n) + 1) * NOBS doubles.
+cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16)
+{
+    const lbm_params &p = ctx->p;
+    ObsArgs O;
+    O.cx = p.probe_center[0];
+    O.cy = p.probe_center[1];
+    O.cz = p.probe_center[2];
+    O.rin2 = p.probe_r_in * p.probe_r_in;
+    O.rout2 = p.probe_r_out * p.probe_r_out;
+    O.G = p.G;
+    const int nb = obs_blocks(ctx->n);
+    double *partial = ctx->red;
+    double *out = ctx->red + (size_t)nb * NOBS;
+    cudaEvent_t e0;
+    prof_begin(ctx, "k_obs_partial", &e0);
+    k_obs_partial<<<nb, OBS_BLOCK, 0, ctx->stream>>>(ctx->dp, O, ctx->type, ctx->phi, ctx->macro, partial);
+    prof_end(ctx, "k_obs_partial", e0);
+    prof_begin(ctx, "k_obs_final", &e0);
+    k_obs_final<<<1, OBS_BLOCK, 0, ctx->stream>>>(partial, nb, out);
+    prof_end(ctx, "k_obs_final", e0);
+    ctx->launches += 2;
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    err = cudaMemcpyAsync(host_out16, out, NOBS * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (err != cudaSuccess) return err;
+    return cudaStreamSynchronize(ctx->stream);
+}
+
+__global__ void k_static_out(int n, const uint8_t *__restrict__ type, const GrayRec *__restrict__ gray,
+                             float *__restrict__ kinv, float *__restrict__ pcs, float *__restrict__ swirr,
+                             float *__restrict__ sores)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    float k6[6] = {0, 0, 0, 0, 0, 0}, p = 0.f, si = 0.f, so = 0.f;
+    if (type[c] == CELL_GRAY) {
+        const GrayRec r = gray[c];
+        const float ik = r.a.w, vx = r.a.x, vy = r.a.y, vz = r.a.z;
+        k6[0] = ik * (1.f + vx * vx);
+        k6[1] = ik * (1.f + vy * vy);
+        k6[2] = ik * (1.f + vz * vz);
+        k6[3] = ik * vx * vy;
+        k6[4] = ik * vx * vz;
+        k6[5] = ik * vy * vz;
+        p = r.b.x;
+        si = r.b.y;
+        so = r.b.z;
+    }
+    if (kinv)
+        for (int k = 0; k < 6; ++k) kinv[(size_t)k * n + c] = k6[k];
+    if (pcs) pcs[c] = p;
+    if (swirr) swirr[c] = si;
+    if (sores) sores[c] = so;
+}
+
+cudaError_t launch_static_out(lbm_ctx *ctx, float *kinv6, float *pcs, float *swirr, float *sores)
+{
+    cudaEvent_t e0;
+    prof_begin(ctx, "k_static_out", &e0);
+    k_static_out<<<(ctx->n + 255) / 256, 256, 0, ctx->stream>>>(ctx->n, ctx->type, ctx->gray, kinv6, pcs,
+                                                                 swirr, sores);
+    prof_end(ctx, "k_static_out", e0);
+    ctx->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,199 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 oracle.
+
+Tolerance: relative 1e-5 in the L2 norm over non-solid cells for rho^A,
+rho^B, u and Sw (FP32 kernels against the FP64 oracle on identical FP32
+inputs).  Geometry results of the FP64 precompute are compared at FP32
+rounding (2e-6 relative).
+"""
+import numpy as np
+import pytest
+
+import lbm_cases as LC
+from helpers import rel_l2
+from paper_2512_21696_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _compare(case, gpu, orc, tol=TOL, what=("rhoA", "rhoB", "u", "sw")):
+    (ga, gb, gu, gs), (oa, ob, ou, osw) = gpu, orc
+    fl = case.cell != synth.SOLID
+    errs = dict(rhoA=rel_l2(ga, oa, fl), rhoB=rel_l2(gb, ob, fl), u=rel_l2(gu, ou, fl), sw=rel_l2(gs, osw, fl))
+    for k in what:
+        assert errs[k] <= tol, f"{case.name}: {k} relative L2 error {errs[k]:.3e} > {tol:.0e} ({errs})"
+    return errs
+
+
+def _compare_static(case, gstat, ostat):
+    kinv, pcs, swirr, sores = gstat
+    gray = case.cell == synth.GRAY
+    if not gray.any():
+        return
+    ok = ostat["kinv"]
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    scale = np.abs(ok).max()
+    for k, (a, b) in enumerate(pairs):
+        np.testing.assert_allclose(kinv[k][gray], ok[a, b][gray], rtol=0, atol=2e-6 * scale)
+    np.testing.assert_allclose(pcs[gray], (ostat["lamL"] * np.array([c["pd"] for c in case.curves])[
+        case.ptype if case.ptype is not None else 0])[gray], rtol=2e-6)
+    np.testing.assert_allclose(swirr[gray], ostat["swirr"][gray], rtol=2e-6, atol=1e-7)
+    np.testing.assert_allclose(sores[gray], ostat["sores"][gray], rtol=2e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize("steps", [1, 10])
+def test_mixed_features_small(steps):
+    case = LC.mixed_features()
+    gf, gobs, gst = LC.run_gpu(case, steps)
+    of, oobs, ost = LC.run_oracle(case, steps)
+    _compare_static(case, gst, ost)
+    _compare(case, gf, of)
+
+
+def test_mixed_features_device_arrays_and_tau():
+    case = LC.mixed_features(seed=7, tau=(0.55, 0.7))
+    gf, _, _ = LC.run_gpu(case, 20, device_arrays=True)
+    of, _, _ = LC.run_oracle(case, 20)
+    _compare(case, gf, of)
+
+
+@pytest.mark.parametrize("shape,periodic", [((5, 7, 13), (1, 1, 1)), ((9, 6, 11), (0, 1, 0)),
+                                            ((1, 17, 33), (1, 0, 1)), ((3, 3, 3), (0, 0, 0))])
+def test_ragged_and_open_boundaries(shape, periodic):
+    case = LC.mixed_features(shape=shape, periodic=periodic, seed=sum(shape))
+    gf, _, gst = LC.run_gpu(case, 12)
+    of, _, ost = LC.run_oracle(case, 12)
+    _compare_static(case, gst, ost)
+    _compare(case, gf, of)
+
+
+def test_droplet_400_steps():
+    """32^3 static droplet (G = 1.1), 400 FP32 steps against the FP64 oracle."""
+    case = LC.droplet()
+    gf, gobs, _ = LC.run_gpu(case, 400)
+    of, oobs, _ = LC.run_oracle(case, 400)
+    errs = _compare(case, gf, of)
+    assert abs(gobs["mass"][0] - oobs["mass"][0]) < 1e-5 * oobs["mass"][0]
+    assert abs(gobs["dp"] - oobs["dp"]) < 1e-4 * abs(oobs["dp"])
+    assert abs(gobs["max_u"] - oobs["max_u"]) < 1e-4 * oobs["max_u"]
+    print("droplet errors", errs)
+
+
+def test_droplet_csf_everywhere_400_steps():
+    case = LC.droplet(kappa=-0.045, csf_everywhere=1)
+    gf, gobs, _ = LC.run_gpu(case, 400)
+    of, oobs, _ = LC.run_oracle(case, 400)
+    _compare(case, gf, of)
+    assert abs(gobs["dp"] - oobs["dp"]) < 1e-3 * abs(oobs["dp"])
+
+
+def test_droplet_regularised_tau():
+    case = LC.droplet(n=24, R=6, tau=(0.55, 0.8))
+    gf, _, _ = LC.run_gpu(case, 200)
+    of, _, _ = LC.run_oracle(case, 200)
+    _compare(case, gf, of)
+
+
+def test_drainage_full_size_two_steps():
+    """The 128^3 multiscale-rock workload of the benchmark, two steps."""
+    case = LC.drainage(128)
+    gf, gobs, gst = LC.run_gpu(case, 2)
+    of, oobs, ost = LC.run_oracle(case, 2)
+    _compare_static(case, gst, ost)
+    _compare(case, gf, of)
+    assert gobs["nan_count"] == 0
+    assert abs(gobs["sat"] - oobs["sat"]) < 1e-6
+
+
+def test_drainage_small_many_steps():
+    case = LC.drainage(32)
+    gf, _, _ = LC.run_gpu(case, 200)
+    of, _, _ = LC.run_oracle(case, 200)
+    _compare(case, gf, of)
+
+
+def test_degenerate_cases():
+    from paper_2512_21696_gb300 import lbm
+    # zero steps: fields are the initial ones
+    case = LC.mixed_features(seed=3)
+    gf, _, _ = LC.run_gpu(case, 0)
+    np.testing.assert_array_equal(gf[0], case.rhoA32 * (case.cell != synth.SOLID))
+    # a single cell
+    one = LC.Case("one", (1, 1, 1), np.zeros((1, 1, 1)), np.ones((1, 1, 1)), np.full((1, 1, 1), 0.7),
+                  np.full((1, 1, 1), 0.2), G=1.1)
+    gf, gobs, _ = LC.run_gpu(one, 5)
+    of, oobs, _ = LC.run_oracle(one, 5)
+    _compare(one, gf, of)
+    # all solid: nothing moves, nothing is non-finite
+    shape = (4, 4, 4)
+    solid = LC.Case("solid", shape, np.full(shape, synth.SOLID), np.zeros(shape), np.ones(shape), np.ones(shape))
+    gf, gobs, _ = LC.run_gpu(solid, 3)
+    assert gobs["nan_count"] == 0 and gobs["mass"] == (0.0, 0.0)
+    # one component only (rho^B = 0)
+    single = LC.Case("single", (6, 6, 6), np.zeros((6, 6, 6)), np.ones((6, 6, 6)), np.ones((6, 6, 6)),
+                     np.zeros((6, 6, 6)), accel=((1e-5, 0, 0), (0, 0, 0)), wet=0)
+    gf, _, _ = LC.run_gpu(single, 30)
+    of, _, _ = LC.run_oracle(single, 30)
+    _compare(single, gf, of, what=("rhoA", "u"))
+
+
+def test_invalid_inputs_are_rejected():
+    from paper_2512_21696_gb300 import lbm
+    case = LC.mixed_features()
+    ctx = lbm.lbm_create(LC.gpu_params(case))
+    try:
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_step(ctx, 1)
+        assert e.value.code == -6
+        bad = case.cell.copy()
+        bad[0, 0, 0] = 7
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_set_geometry(ctx, bad, case.phi32)
+        badphi = case.phi32.copy()
+        badphi[case.cell == synth.GRAY] = 1.5
+        if (case.cell == synth.GRAY).any():
+            with pytest.raises(lbm.LbmError):
+                lbm.lbm_set_geometry(ctx, case.cell, badphi)
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_set_constitutive(ctx, 16, lbm.lbm_default_constitutive())
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_set_constitutive(ctx, 0, lbm.lbm_default_constitutive(aniso=0.5))
+    finally:
+        ctx.close()
+    p = LC.gpu_params(case)
+    p.tau[0] = 0.5
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_create(p)
+
+
+def test_checkpoint_roundtrip_is_bit_exact():
+    from paper_2512_21696_gb300 import lbm
+    case = LC.mixed_features(seed=11)
+    ctx = lbm.lbm_create(LC.gpu_params(case))
+    try:
+        for k, cv in enumerate(case.curves):
+            lbm.lbm_set_constitutive(ctx, k, lbm.lbm_default_constitutive(
+                kc_d=cv["kc_d"], pd=cv["pd"], lam=cv["lam"], swr=cv["swr"], nw=cv["nw"], nn=cv["nn"],
+                phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"]))
+        lbm.lbm_set_geometry(ctx, case.cell, case.phi32, case.ptype)
+        lbm.lbm_init_fields(ctx, case.rhoA32, case.rhoB32, case.u32)
+        lbm.lbm_step(ctx, 7)
+        state = lbm.lbm_save_state(ctx)
+        lbm.lbm_step(ctx, 9)
+        a = [x.copy() for x in lbm.lbm_get_fields(ctx)]
+        lbm.lbm_load_state(ctx, state)
+        lbm.lbm_step(ctx, 9)
+        b = lbm.lbm_get_fields(ctx)
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+        assert lbm.lbm_observables(ctx)["step"] == 16
+    finally:
+        ctx.close()
+
+
+def test_mass_conservation_fp32():
+    case = LC.drainage(48)
+    gf0, g0, _ = LC.run_gpu(case, 0)
+    gf, g1, _ = LC.run_gpu(case, 300)
+    for a in range(2):
+        assert abs(g1["mass"][a] - g0["mass"][a]) < 2e-6 * g0["mass"][a]
