@@ -93,7 +93,8 @@ typedef struct lbm_params {
     double rho_hi, rho_lo;  /* bulk majority / minority densities */
     double s_lo, s_hi;      /* residual hysteresis thresholds on s */
     double at_cut;          /* H(At) = |grad At|/2 only where |At| <= at_cut */
-    double eps_n;           /* floor of |grad| in unit normals */
+    double eps_n;           /* floor of |grad| in unit normals (default 1e-4 rho_hi:
+                               keeps Eq. 4's normals well defined in FP32) */
     double kr_min;          /* floor of relative permeabilities */
     double c_g;             /* weight of grad(phi) grad(phi)^T in the axis tensor */
     int storage;            /* enum lbm_storage */
@@ -156,7 +157,7 @@ LBM_API int lbm_abi_version(void);
 /* Fill p with defaults for an nx*ny*nz periodic grid: tau = 1, G = 0,
  * kappa_csf = 0, rho_hi/lo = 1/0.03, phi_avg = (rho_hi+rho_lo)/2,
  * phi_max = rho_hi, rho_wall = (rho_hi+rho_lo)/2 (neutral wetting),
- * wet_idx = 1, s_lo/s_hi = 0.1/0.9, at_cut = 0.95, eps_n = 1e-8 rho_hi,
+ * wet_idx = 1, s_lo/s_hi = 0.1/0.9, at_cut = 0.95, eps_n = 1e-4 rho_hi,
  * kr_min = 1e-6, c_g = 1, F32 storage, NULL stream, probe at the grid
  * centre with r_in = 0, r_out = +inf.  LBM_ERR_ARG if p is NULL or a size
  * is < 1. */
@@ -168,7 +169,7 @@ LBM_API int lbm_default_params(lbm_params *p, int nx, int ny, int nz);
 LBM_API int lbm_default_constitutive(lbm_constitutive *c);
 
 /* Create a context on the current CUDA device.  Validates p (sizes >= 1,
- * tau > 1/2, rho_hi > rho_lo > 0 ... ; LBM_ERR_ARG otherwise) and allocates
+ * tau > 1/2, 4 >= rho_hi > rho_lo > 0 ... ; LBM_ERR_ARG otherwise) and allocates
  * the population, density, field and geometry buffers (LBM_ERR_OOM if the
  * device is too small).  *out is NULL on failure.  Every pore type starts
  * with the default curves. */

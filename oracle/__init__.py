@@ -142,7 +142,7 @@ def make_params(shape, **kw) -> OrcParams:
     p.s_lo = kw.pop("s_lo", 0.1)
     p.s_hi = kw.pop("s_hi", 0.9)
     p.at_cut = kw.pop("at_cut", 0.95)
-    p.eps_n = kw.pop("eps_n", 1e-8 * rho_hi)
+    p.eps_n = kw.pop("eps_n", 1e-4 * rho_hi)
     p.kr_min = kw.pop("kr_min", 1e-6)
     p.c_g = kw.pop("c_g", 1.0)
     if kw:

@@ -78,6 +78,7 @@ void fill_device_params(lbm_ctx *ctx)
         for (int k = 0; k < 3; ++k) d.accel[a][k] = (float)p.body_accel[a][k];
     }
     d.G = (float)p.G;
+    d.G_lo = (float)(p.G - (double)d.G);
     d.kappa = (float)p.kappa_csf;
     d.csf_everywhere = p.csf_everywhere ? 1 : 0;
     d.wet = p.wet_idx;
@@ -189,7 +190,7 @@ int lbm_default_params(lbm_params *p, int nx, int ny, int nz)
     p->s_lo = 0.1;
     p->s_hi = 0.9;
     p->at_cut = 0.95;
-    p->eps_n = 1e-8 * p->rho_hi;
+    p->eps_n = 1e-4 * p->rho_hi;
     p->kr_min = 1e-6;
     p->c_g = 1.0;
     p->storage = LBM_STORAGE_F32;
@@ -226,7 +227,7 @@ int lbm_create(lbm_ctx **out, const lbm_params *p)
     const long long n = (long long)p->nx * p->ny * p->nz;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || n > (long long)INT32_MAX / 8) return LBM_ERR_ARG;
     if (!(p->tau[0] > 0.5 && p->tau[1] > 0.5)) return LBM_ERR_ARG;
-    if (!(p->rho_hi > p->rho_lo && p->rho_lo > 0.0)) return LBM_ERR_ARG;
+    if (!(p->rho_hi > p->rho_lo && p->rho_lo > 0.0 && p->rho_hi <= 4.0)) return LBM_ERR_ARG;
     if (!(p->phi_avg[0] > 0 && p->phi_avg[1] > 0 && p->phi_max[0] > 0 && p->phi_max[1] > 0)) return LBM_ERR_ARG;
     if (p->wet_idx != 0 && p->wet_idx != 1) return LBM_ERR_ARG;
     if (!(p->s_lo >= 0 && p->s_lo < p->s_hi && p->s_hi <= 1)) return LBM_ERR_ARG;

@@ -55,7 +55,7 @@ struct DevParams {
     int n;                 // number of cells
     float omega_fac[2];    // 1 - 1/tau
     float nu[2];           // (tau - 1/2)/3
-    float G;
+    float G, G_lo;         // Shan-Chen coupling as float-float
     float kappa;
     float csf_coef[2];     // 1 / (phi_avg * phi_max)
     int csf_everywhere;

@@ -12,9 +12,8 @@
 //   K0 (Kozeny-Carman), Leverett factor lamL (Eq. 5), and the residual
 //   amounts from the crossings of Pc(Sw; phi) with pc_ref_max_f*pd and
 //   pc_ref_min_f*pd (Fig. 6).
-// The eigenvalues come from the closed-form trigonometric solution of the
-// characteristic cubic (Smith, 1961) and e1 from the largest cross product of
-// two rows of M - mu1 I.
+// The eigen-decomposition uses cyclic Jacobi rotations in FP64, which keep
+// exact ties exact (grid-aligned neighbourhoods often give them).
 #include <cmath>
 
 #include "lbm_context.h"
@@ -46,44 +45,51 @@ __device__ __forceinline__ double kozeny(const lbm_constitutive &cv, double phi)
     return cv.kc_d * cv.kc_d * phi * phi * phi / (180.0 * (1.0 - phi) * (1.0 - phi));
 }
 
-// Top eigenvector of a symmetric 3x3 matrix; returns false on a tie.
-__device__ bool top_eigvec(const double M[3][3], double e[3])
+// Top eigenvector of a symmetric 3x3 matrix by cyclic Jacobi rotations
+// (Rutishauser's formulation); returns false when the two largest
+// eigenvalues tie (mu1 - mu2 <= 1e-12 mu1), i.e. no preferred axis.
+__device__ bool top_eigvec(const double Min[3][3], double e[3])
 {
-    const double p1 = M[0][1] * M[0][1] + M[0][2] * M[0][2] + M[1][2] * M[1][2];
-    const double q = (M[0][0] + M[1][1] + M[2][2]) / 3.0;
-    const double d0 = M[0][0] - q, d1 = M[1][1] - q, d2 = M[2][2] - q;
-    const double p2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * p1;
-    const double p = sqrt(p2 / 6.0);
-    if (!(p > 0.0)) return false;
-    const double B00 = d0 / p, B11 = d1 / p, B22 = d2 / p;
-    const double B01 = M[0][1] / p, B02 = M[0][2] / p, B12 = M[1][2] / p;
-    const double det = B00 * (B11 * B22 - B12 * B12) - B01 * (B01 * B22 - B12 * B02) +
-                       B02 * (B01 * B12 - B11 * B02);
-    double r = 0.5 * det;
-    r = r < -1.0 ? -1.0 : (r > 1.0 ? 1.0 : r);
-    const double ang = acos(r) / 3.0;
-    const double mu1 = q + 2.0 * p * cos(ang);
-    const double mu3 = q + 2.0 * p * cos(ang + 2.0943951023931954923);  // + 2 pi/3
-    const double mu2 = 3.0 * q - mu1 - mu3;
-    if (mu1 - mu2 <= 1e-12 * fmax(mu1, 1e-30)) return false;
-    const double R[3][3] = {{M[0][0] - mu1, M[0][1], M[0][2]},
-                            {M[1][0], M[1][1] - mu1, M[1][2]},
-                            {M[2][0], M[2][1], M[2][2] - mu1}};
-    double best[3] = {0, 0, 0}, bn = 0.0;
-    for (int a = 0; a < 3; ++a)
-        for (int b = a + 1; b < 3; ++b) {
-            const double cr[3] = {R[a][1] * R[b][2] - R[a][2] * R[b][1],
-                                  R[a][2] * R[b][0] - R[a][0] * R[b][2],
-                                  R[a][0] * R[b][1] - R[a][1] * R[b][0]};
-            const double nn = cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2];
-            if (nn > bn) {
-                bn = nn;
-                best[0] = cr[0]; best[1] = cr[1]; best[2] = cr[2];
-            }
+    double A[3][3], V[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            A[r][c] = Min[r][c];
+            V[r][c] = (r == c) ? 1.0 : 0.0;
         }
-    if (!(bn > 0.0)) return false;
-    const double inv = 1.0 / sqrt(bn);
-    for (int d = 0; d < 3; ++d) e[d] = best[d] * inv;
+    for (int sweep = 0; sweep < 32; ++sweep) {
+        const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+        const double dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+        if (off == 0.0 || off <= 1e-34 * dia) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                const double apq = A[p][q];
+                if (apq == 0.0) continue;
+                const double theta = 0.5 * (A[q][q] - A[p][p]) / apq;
+                const double t = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / sqrt(t * t + 1.0), sn = t * cs, tau = sn / (1.0 + cs);
+                const int r = 3 - p - q;  // the third index
+                const double arp = A[r][p], arq = A[r][q];
+                A[p][p] -= t * apq;
+                A[q][q] += t * apq;
+                A[p][q] = A[q][p] = 0.0;
+                A[r][p] = A[p][r] = arp - sn * (arq + tau * arp);
+                A[r][q] = A[q][r] = arq + sn * (arp - tau * arq);
+                for (int k = 0; k < 3; ++k) {
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = vkp - sn * (vkq + tau * vkp);
+                    V[k][q] = vkq + sn * (vkp - tau * vkq);
+                }
+            }
+    }
+    int top = 0;
+    for (int k = 1; k < 3; ++k)
+        if (A[k][k] > A[top][top]) top = k;
+    double second = -INFINITY;
+    for (int k = 0; k < 3; ++k)
+        if (k != top && A[k][k] > second) second = A[k][k];
+    const double mu1 = A[top][top];
+    if (mu1 - second <= 1e-12 * fmax(mu1, 1e-30)) return false;
+    for (int d = 0; d < 3; ++d) e[d] = V[d][top];
     return true;
 }
 

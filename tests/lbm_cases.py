@@ -33,7 +33,7 @@ class Case:
         self.curves = curves or [dict(CURVE)]
         self.s = dict(DEFAULTS)
         self.s.update(settings)
-        self.s["eps_n"] = settings.get("eps_n", 1e-8 * self.s["rho_hi"])
+        self.s["eps_n"] = settings.get("eps_n", 1e-4 * self.s["rho_hi"])
         self.probe = settings.get("probe", (0.5 * (shape[2] - 1), 0.5 * (shape[1] - 1),
                                             0.5 * (shape[0] - 1), 0.0, 1e30))
         self.s.pop("probe", None)

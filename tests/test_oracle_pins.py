@@ -484,7 +484,7 @@ def _bruteforce_case(seed, csf_everywhere, tau):
                  f_min=0.575, aniso=10.0)
     o = O.Oracle(O.make_params(shape, **common), cell, phi, curves=[O.make_curve(lam=2.0, **curve)])
     pd = dict(common, rho_hi=1.0, rho_lo=0.03, phi_avg=(0.515, 0.515), phi_max=(1.0, 1.0),
-              s_lo=0.1, s_hi=0.9, at_cut=0.95, eps_n=1e-8, kr_min=1e-6)
+              s_lo=0.1, s_hi=0.9, at_cut=0.95, eps_n=1e-4, kr_min=1e-6)
     nv = N.NaiveLBM(pd, cell, phi, curve={**curve, "lambda": 2.0})
     o.init_fields(ra, rb, u0)
     nv.init(ra, rb, u0)
