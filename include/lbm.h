@@ -232,6 +232,30 @@ LBM_API int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *c
 /* Number of kernels the context has launched since creation. */
 LBM_API int lbm_launch_count(lbm_ctx *ctx, long long *count);
 
+/* Observables of caller-provided fields, without allocating.  The paper has
+ * no counterpart: this is a service for callers that cannot call cudaMalloc
+ * (host callbacks and allocator hooks, plug-ins whose host application owns
+ * the device memory pool, loops that must not risk an allocation's implicit
+ * synchronisation).  It computes what lbm_observables computes, from
+ *   fields    device [6][ncell] float: rhoA, rhoB, ux, uy, uz, Sw (the layout
+ *             lbm_get_fields writes when given one buffer's consecutive rows),
+ *   type      device [ncell] cell codes, phi device [ncell] porosity,
+ *   probe     host {cx, cy, cz, r_in, r_out} of the pressure probe, G the
+ *             Shan-Chen coupling of the pressure p = (rhoA+rhoB)/3 + G rhoA rhoB,
+ * on `stream` (cudaStream_t, NULL = legacy default), and writes *out (host;
+ * out->step is 0).  Synchronises the stream.
+ * Scratch: a file-scope device array of 131,200 bytes that every GPU loading
+ * this library holds until exit.  The first call on a device resolves that
+ * array's address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * race.  Nothing is allocated, freed, or needs clearing between calls.
+ * Errors: LBM_ERR_ARG for NULL pointers, sizes < 1 or more than
+ * LBM_NOALLOC_MAX_CELLS cells; LBM_ERR_CUDA; LBM_ERR_NUMERIC when non-finite
+ * values were found (out is still filled). */
+#define LBM_NOALLOC_MAX_CELLS (1LL << 28)
+LBM_API int lbm_observables_noalloc(const float *fields, const uint8_t *type, const float *phi, int nx, int ny,
+                                    int nz, double G, const double probe[5], void *stream, lbm_obs *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,20 +8,9 @@
 #include <cfloat>
 
 #include "lbm_context.h"
+#include "lbm_obs.cuh"
 
 namespace lbm {
-
-constexpr int NOBS = 16;
-// slots: 0,1 mass; 2 sum phi_c Sw; 3 sum phi_c; 4 outlet u_x; 5..7 sum u;
-//        8 max |u|; 9 sum p inside; 10 count inside; 11 sum p outside;
-//        12 count outside; 13 non-finite count
-constexpr int SLOT_MAX = 8;
-constexpr int OBS_BLOCK = 256;
-constexpr int OBS_MAX_BLOCKS = 1024;
-
-struct ObsArgs {
-    double cx, cy, cz, rin2, rout2, G;
-};
 
 __device__ __forceinline__ double warp_sum(double v)
 {

@@ -20,7 +20,7 @@ __all__ = [
     "LbmError", "LbmContext", "lbm_default_params", "lbm_default_constitutive", "lbm_create",
     "lbm_destroy", "lbm_set_constitutive", "lbm_set_geometry", "lbm_init_fields", "lbm_step",
     "lbm_observables", "lbm_get_fields", "lbm_get_static", "lbm_save_state", "lbm_load_state",
-    "lbm_profile", "lbm_profile_read", "lbm_launch_count", "lbm_abi_version",
+    "lbm_profile", "lbm_profile_read", "lbm_launch_count", "lbm_abi_version", "lbm_observables_noalloc",
     "LBM_CELL_PORE", "LBM_CELL_SOLID", "LBM_CELL_GRAY", "LBM_STORAGE_F32", "LBM_STORAGE_F16S",
     "LBM_STORAGE_BF16S",
 ]
@@ -241,3 +241,31 @@ def lbm_launch_count(ctx: LbmContext) -> int:
     c = C.c_longlong()
     _check(L.load().lbm_launch_count(ctx.handle, C.byref(c)), "lbm_launch_count")
     return c.value
+
+
+def lbm_observables_noalloc(fields, cell_type, phi, shape, G, probe, stream=None, check: bool = True) -> dict:
+    """Observables of caller-owned device fields without any device allocation.
+
+    For callers that cannot allocate device memory (host callbacks, allocator
+    hooks, plug-ins whose application owns the memory pool).  `fields` is a
+    device float32 array of 6*ncell values (rhoA, rhoB, ux, uy, uz, Sw rows),
+    `cell_type` uint8 and `phi` float32 device arrays of ncell values, `shape`
+    (nz, ny, nx), `probe` (cx, cy, cz, r_in, r_out).  The library's shared
+    device scratch is used, so concurrent calls on different streams race.
+    """
+    nz, ny, nx = shape
+    n = nx * ny * nz
+    for a in (fields, cell_type, phi):
+        if not _is_device(a):
+            raise TypeError("lbm_observables_noalloc takes device arrays only")
+    keep = []
+    pr = (C.c_double * 5)(*[float(v) for v in probe])
+    o = L.lbm_obs()
+    s = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    code = L.load().lbm_observables_noalloc(_ptr(fields, np.float32, 6 * n, keep), _ptr(cell_type, np.uint8, n, keep),
+                                            _ptr(phi, np.float32, n, keep), int(nx), int(ny), int(nz), float(G), pr,
+                                            s, C.byref(o))
+    if code not in (L.LBM_OK, L.LBM_ERR_NUMERIC) or (check and code != L.LBM_OK):
+        raise LbmError(code, "lbm_observables_noalloc")
+    return dict(mass=(o.mass[0], o.mass[1]), sat=o.sat, flux_out=o.flux_out,
+                flux_vol=tuple(o.flux_vol), max_u=o.max_u, dp=o.dp, nan_count=o.nan_count, step=o.step)
