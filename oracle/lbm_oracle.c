@@ -20,8 +20,12 @@
  *     reading of Eq. 3 with u = (j + F/2)/rho).
  *   - Shan-Chen inter-component force with psi = rho (Sec. II, refs. [15,16]);
  *     solid neighbours carry virtual wall densities rho_wall.
- *   - CSF surface-tension control, Eq. 4, with phi^a = rho^{other};
- *     unit normals are zero at solid and outside cells.
+ *   - CSF surface-tension control, Eq. 4, with phi^a = rho^{other}.  Reading
+ *     of the divergence of the unit normal: with g = grad phi, H its Hessian
+ *     and the regularised normal n = g / s, s = sqrt(|g|^2 + eps_n^2),
+ *     div n = tr(H)/s - g.H.g / s^3 (curvature identity), evaluated with the
+ *     isotropic D3Q19 gradient and the D3Q19 moment Hessian of the cell's own
+ *     neighbourhood (solid neighbours carry rho_wall).
  *   - Multiscale force of Eq. 1 in gray cells: capillary term
  *     -Pc(Sw) rho_r n H and the viscous resistance, the latter made tensorial
  *     by Eqs. 6-7 (principal axis from the Hessian and gradient of porosity,
@@ -34,7 +38,7 @@
  *     Pc(Sw), Corey Kr(Sw).
  *
  * Order inside one step: stream; moments at all cells; residual update;
- * density gradients and normals at all cells; forces and velocity; collide.
+ * density gradients at all cells; forces and velocity; collide.
  * Every force reads neighbour densities of the same time level.
  */
 #include <math.h>
@@ -112,7 +116,7 @@ typedef struct orc_state {
     double *f, *fs;
     /* fields of the last step */
     double *rho[2], *j, *u, *sw, *s;
-    double *grad[2], *nhat[2];
+    double *grad[2];
     double *term[N_TERM][2];
     double *F[2];
     long steps;
@@ -234,6 +238,23 @@ static void jacobi3(double A[3][3], double evals[3], double V[3][3])
         }
     }
     for (int k = 0; k < 3; ++k) evals[k] = A[k][k];
+}
+
+/* Hessian of the density of component a at fluid cell c from the lattice
+ * moments: since sum_i w_i (c_i c_i - cs^2 I) c_i c_i : X = 2 cs^4 X for
+ * symmetric X on D3Q19, H = (1/cs^4) sum_i w_i (c_i c_i - cs^2 I)
+ * (rho(x + c_i) - rho(x)), solid neighbours carrying rho_wall. */
+static void density_hessian(const orc_state *st, long c, int a, double H[3][3])
+{
+    double fc = st->rho[a][c];
+    for (int d = 0; d < 3; ++d)
+        for (int e = 0; e < 3; ++e) H[d][e] = 0.0;
+    for (int i = 1; i < 19; ++i) {
+        double df = rho_seen(st, neighbour(st, c, CV[i][0], CV[i][1], CV[i][2]), a) - fc;
+        for (int d = 0; d < 3; ++d)
+            for (int e = 0; e < 3; ++e)
+                H[d][e] += weight(i) * (CV[i][d] * CV[i][e] - (d == e ? CS2 : 0.0)) * df / (CS2 * CS2);
+    }
 }
 
 /* Geometry precompute for gray cell c (Eqs. 5-7). */
@@ -411,7 +432,7 @@ void orc_destroy(orc_state *st)
     free(st->iso); free(st->Rw); free(st->Ro); free(st->wetflag);
     free(st->f); free(st->fs);
     for (int a = 0; a < 2; ++a) {
-        free(st->rho[a]); free(st->grad[a]); free(st->nhat[a]); free(st->F[a]);
+        free(st->rho[a]); free(st->grad[a]); free(st->F[a]);
         for (int t = 0; t < N_TERM; ++t) free(st->term[t][a]);
     }
     free(st->j); free(st->u); free(st->sw); free(st->s);
@@ -445,7 +466,7 @@ orc_state *orc_create(const orc_params *p, const orc_curve *curves, int ncurve,
     st->f = alloc0(2 * 19 * n);
     st->fs = alloc0(2 * 19 * n);
     for (int a = 0; a < 2; ++a) {
-        st->rho[a] = alloc0(n); st->grad[a] = alloc0(3 * n); st->nhat[a] = alloc0(3 * n);
+        st->rho[a] = alloc0(n); st->grad[a] = alloc0(3 * n);
         st->F[a] = alloc0(3 * n);
         for (int t = 0; t < N_TERM; ++t) st->term[t][a] = alloc0(3 * n);
     }
@@ -570,7 +591,7 @@ static void one_step(orc_state *st)
         }
     }
 
-    /* (4a) gradient of phi^a = rho^{other} and its unit normal at every fluid cell */
+    /* (4a) gradient of phi^a = rho^{other} at every fluid cell */
 #pragma omp parallel for schedule(static)
     for (long c = 0; c < n; ++c) {
         for (int a = 0; a < 2; ++a) {
@@ -582,12 +603,7 @@ static void one_step(orc_state *st)
                     for (int d = 0; d < 3; ++d) g[d] += weight(i) * v * CV[i][d] / CS2;
                 }
             }
-            double mag = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-            double den = fmax(mag, p->eps_n);
-            for (int d = 0; d < 3; ++d) {
-                st->grad[a][d * n + c] = g[d];
-                st->nhat[a][d * n + c] = st->type[c] == SOLID ? 0.0 : g[d] / den;
-            }
+            for (int d = 0; d < 3; ++d) st->grad[a][d * n + c] = g[d];
         }
     }
 
@@ -616,13 +632,16 @@ static void one_step(orc_state *st)
                 T[T_BODY][a][d] = r[a] * p->accel[a][d];
             }
             if (p->kappa != 0.0 && (p->csf_everywhere || gray)) {
-                /* Eq. 4: kappa (-div n^a) (grad phi^a / phi_avg) (rho^a / phi_max) */
-                double div = 0.0;
-                for (int i = 0; i < 19; ++i) {
-                    long m = neighbour(st, c, CV[i][0], CV[i][1], CV[i][2]);
-                    if (is_wall(st, m)) continue;
-                    for (int d = 0; d < 3; ++d) div += weight(i) * st->nhat[a][d * n + m] * CV[i][d] / CS2;
-                }
+                /* Eq. 4: kappa (-div n^a) (grad phi^a / phi_avg) (rho^a / phi_max),
+                 * div n = tr(H)/s - g.H.g/s^3, s = sqrt(|g|^2 + eps_n^2) */
+                double H[3][3], g[3];
+                density_hessian(st, c, 1 - a, H);
+                for (int d = 0; d < 3; ++d) g[d] = st->grad[a][d * n + c];
+                double s = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2] + p->eps_n * p->eps_n);
+                double gHg = 0.0;
+                for (int d = 0; d < 3; ++d)
+                    for (int e = 0; e < 3; ++e) gHg += g[d] * H[d][e] * g[e];
+                double div = (H[0][0] + H[1][1] + H[2][2]) / s - gHg / (s * s * s);
                 for (int d = 0; d < 3; ++d)
                     T[T_CSF][a][d] = p->kappa * (-div) * (st->grad[a][d * n + c] / p->phi_avg[a]) *
                                      (r[a] / p->phi_max[a]);

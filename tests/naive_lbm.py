@@ -58,6 +58,20 @@ def iso_grad(field):
     return out
 
 
+def moment_hessian(field_seen, field_center):
+    """(1/cs^4) sum_i w_i (c_i c_i - cs^2 I)(field(x + c_i) - field(x))."""
+    H = np.zeros((3, 3) + field_seen.shape, dtype=field_seen.dtype)
+    for i in range(1, 19):
+        c = VEL[i]
+        diff = shift_to(field_seen, c) - field_center
+        for a in range(3):
+            for b in range(3):
+                q = c[a] * c[b] - (CS2 if a == b else 0.0)
+                if q != 0.0:
+                    H[a, b] += WGT[i] * q * diff / (CS2 * CS2)
+    return H
+
+
 def kozeny_carman(d, phi):
     return d * d * phi ** 3 / (180.0 * (1.0 - phi) ** 2)
 
@@ -198,13 +212,12 @@ class NaiveLBM:
             body = rho[a][None] * np.asarray(p["accel"][a], dt)[:, None, None, None]
             csf = np.zeros_like(sc)
             if p["kappa"] != 0.0:
-                mag = np.sqrt((grad[a] ** 2).sum(axis=0))
-                nh = np.where(self.solid[None], 0.0, grad[a] / np.maximum(mag, p["eps_n"]))
-                div = np.zeros(self.cell.shape, dt)
-                for i in range(1, 19):
-                    for d in range(3):
-                        if VEL[i][d]:
-                            div += WGT[i] * VEL[i][d] * shift_to(nh[d], VEL[i]) / CS2
+                # div of g/sqrt(|g|^2 + eps^2) = tr(H)/s - g.H.g/s^3, H = Hessian of phi^a
+                H = moment_hessian(seen[1 - a], rho[1 - a])
+                g = grad[a]
+                s = np.sqrt((g ** 2).sum(axis=0) + p["eps_n"] ** 2)
+                gHg = np.einsum("a...,ab...,b...->...", g, H, g)
+                div = (H[0, 0] + H[1, 1] + H[2, 2]) / s - gHg / s ** 3
                 mask = np.ones(self.cell.shape, bool) if p["csf_everywhere"] else self.gray
                 csf = np.where(mask[None], p["kappa"] * (-div)[None] * (grad[a] / p["phi_avg"][a])
                                * (rho[a] / p["phi_max"][a])[None], 0.0)

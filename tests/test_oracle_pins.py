@@ -262,9 +262,10 @@ def test_csf_force_on_cylinder_matches_continuum():
     """Eq. 4 on a smooth cylindrical interface: div n = 1/r in two dimensions.
 
     phi^A = rho^B = b0 + b1 tanh((r - R)/w) rises outward, so n^A = r-hat and
-    F_csf^A,r = kappa (-1/r) (d rho^B/dr / phi_avg) (rho^A / phi_max).
+    F_csf^A,r = kappa (-1/r) (d rho^B/dr / phi_avg) (rho^A / phi_max).  The
+    lattice stencils carry an O((1/w)^2) truncation error (0.8 % at w = 8).
     """
-    n, R, w = 96, 30.0, 5.0
+    n, R, w = 128, 40.0, 8.0
     shape = (1, n, n)
     y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     cx = cy = n / 2 - 0.5
@@ -282,7 +283,7 @@ def test_csf_force_on_cylinder_matches_continuum():
     cont = kappa * (-1.0 / r) * (dBdr / 0.515) * (rhoA[0] / 1.0)
     band = np.abs(r - R) < 1.0
     rel = np.abs(Fr[band] - cont[band]) / np.abs(cont[band])
-    assert rel.max() < 0.03
+    assert rel.max() < 0.02
     assert np.all(np.sign(Fr[band]) == np.sign(cont[band]))
 
 
