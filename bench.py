@@ -56,6 +56,7 @@ def algorithmic_bytes(cell):
     gray = int((cell == 2).sum())
     step = fluid * 304 + n * 1 + gray * 25
     return dict(step=step,
+                k_fused=fluid * 304 + n * 1 + gray * 32,
                 k_collide=fluid * 304 + n * 1 + n * 8 + gray * 32,
                 k_density=fluid * 152 + n * 1 + n * 8), fluid, gray
 
@@ -165,6 +166,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     p = lbm.lbm_default_params(nx, ny, nz, stream=stream.cuda_stream, **SETTINGS)
     ctx = lbm.lbm_create(p)
+    lbm.lbm_set_kernel(ctx, args.path, args.tile)
     lbm.lbm_set_constitutive(ctx, 0, lbm.lbm_default_constitutive())
     dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in inp.items()}
     lbm.lbm_set_geometry(ctx, dev["cell"], dev["phi"], dev["ptype"])
@@ -335,6 +337,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--path", type=int, default=0, help="0 fused single launch, 1 two launches")
+    ap.add_argument("--tile", type=int, default=0, help="fused tile: 0 = 32x8, 1 = 32x16")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -229,6 +229,14 @@ LBM_API int lbm_load_state(lbm_ctx *ctx, const void *host_buf, size_t bytes);
 LBM_API int lbm_profile(lbm_ctx *ctx, int enable);
 LBM_API int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *count);
 
+/* Kernel path of lbm_step: path 0 (default) = one fused launch per step
+ * (rolling z-window with shared-memory halos), path 1 = two launches
+ * (densities, then forces + collision).  tile selects the fused tile:
+ * 0 = 32x8 columns, 1 = 32x16, 2 = 32x8 with two CTAs per SM.  Both paths
+ * compute identical states.
+ * LBM_ERR_ARG on unknown values. */
+LBM_API int lbm_set_kernel(lbm_ctx *ctx, int path, int tile);
+
 /* Number of kernels the context has launched since creation. */
 LBM_API int lbm_launch_count(lbm_ctx *ctx, long long *count);
 

@@ -82,7 +82,7 @@ EXPORTS = [
     "lbm_default_constitutive", "lbm_create", "lbm_destroy", "lbm_set_constitutive",
     "lbm_set_geometry", "lbm_init_fields", "lbm_step", "lbm_observables", "lbm_get_fields",
     "lbm_get_static", "lbm_state_size", "lbm_save_state", "lbm_load_state", "lbm_profile",
-    "lbm_profile_read", "lbm_launch_count", "lbm_struct_size", "lbm_observables_noalloc",
+    "lbm_profile_read", "lbm_launch_count", "lbm_struct_size", "lbm_observables_noalloc", "lbm_set_kernel",
 ]
 
 _lock = threading.Lock()
@@ -129,6 +129,7 @@ def load(build_if_needed: bool = True):
         lib.lbm_launch_count.argtypes = [P, C.POINTER(C.c_longlong)]
         lib.lbm_observables_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_double,
                                                 C.POINTER(C.c_double), vp, C.POINTER(lbm_obs)]
+        lib.lbm_set_kernel.argtypes = [P, C.c_int, C.c_int]
         lib.lbm_struct_size.restype = C.c_size_t
         lib.lbm_struct_size.argtypes = [C.c_int]
         for name in EXPORTS:

@@ -372,8 +372,12 @@ int lbm_step(lbm_ctx *ctx, int nsteps)
     DeviceGuard g(ctx->dev);
     if (!g.ok) return LBM_ERR_CUDA;
     for (int k = 0; k < nsteps; ++k) {
-        LBM_CUDA(lbm::launch_density(ctx));
-        LBM_CUDA(lbm::launch_collide(ctx, k == nsteps - 1));
+        if (ctx->path == 1) {
+            LBM_CUDA(lbm::launch_density(ctx));
+            LBM_CUDA(lbm::launch_collide(ctx, k == nsteps - 1));
+        } else {
+            LBM_CUDA(lbm::launch_fused(ctx, k == nsteps - 1));
+        }
         ctx->steps += 1;
     }
     return LBM_OK;
@@ -538,6 +542,14 @@ int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *count)
     }
     *count = (int)acc.size();
     for (int k = 0; k < max && k < (int)acc.size(); ++k) out[k] = acc[k];
+    return LBM_OK;
+}
+
+int lbm_set_kernel(lbm_ctx *ctx, int path, int tile)
+{
+    if (!ctx || path < 0 || path > 1 || tile < 0 || tile > 2) return LBM_ERR_ARG;
+    ctx->path = path;
+    ctx->tile = tile;
     return LBM_OK;
 }
 

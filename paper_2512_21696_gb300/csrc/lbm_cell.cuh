@@ -1,0 +1,389 @@
+// Per-cell arithmetic of the time step, shared by the two-launch path
+// (k_density + k_collide) and the fused rolling-window kernel, so that both
+// compute bit-identical states.
+//
+// Storage convention (F32), push form: the buffer holds the streamed
+// (pre-collision) state.  Per component, slot 0 of cell x is the rest
+// population f_0(x) in 2^-30 fixed point (int32); slot i (1..18) of x holds
+// g_i = f_i(x) - 3 w_i f_0(s) in FP32, the population that arrived from the
+// source s = x - c_i relative to the source's rest population (s = x itself
+// after a bounce-back at a solid source).  Relative to the cell's own rest
+// population the arrived population is h_i = g_i + w3_i (f_0(s) - f_0(x)),
+// w3_i = 3 w_i.  The g parts are summed in FP32; the rest-population parts
+// exactly in 64-bit integers with weights 12 w3_i (2 on faces, 1 on edges) and
+// converted once.  Each cell reads only its own slots (coalesced) and writes
+// its post-collision populations into the slots of its neighbours.
+#pragma once
+
+#include "lbm_common.cuh"
+
+namespace lbm {
+
+constexpr float FIX_ONE = 1073741824.0f;          // 2^30
+constexpr float FIX_INV = 9.313225746154785e-10f;  // 2^-30
+constexpr double FIX_ONE_D = 1073741824.0;
+
+// 3 w_i for the moving populations (faces 1/6, edges 1/12).
+__host__ __device__ constexpr float w3(int i) { return i <= 6 ? (1.0f / 6.0f) : (1.0f / 12.0f); }
+// 12 w3_i: the integer weight of a rest-population difference.
+__host__ __device__ constexpr int w12(int i) { return i <= 6 ? 2 : 1; }
+
+// Difference of two fixed-point rest populations, as a float.
+__device__ __forceinline__ float fix_diff(int a, int b) { return (float)(a - b) * FIX_INV; }
+
+// ---- float-float (unevaluated sum hi + lo) arithmetic ----------------------
+// Used where physically large, nearly cancelling terms meet: at interfaces the
+// Shan-Chen force (~0.1) balances the pressure part of j (~0.05) and u is
+// their O(1e-3) residual.  Error-free transformations of Knuth (two-sum) and
+// Dekker (fast two-sum) and FMA-based products.
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y)
+{
+    const ff s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ ff ff_add_f(ff x, float y)
+{
+    const ff s = two_sum(x.hi, y);
+    return fast_two_sum(s.hi, s.lo + x.lo);
+}
+__device__ __forceinline__ ff ff_mul(ff x, ff y)
+{
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_scale(ff x, float pow2) { return {x.hi * pow2, x.lo * pow2}; }
+// Exact value v * pow2 of an integer (|v| < 2^47) as float-float: the upper
+// and lower 24-bit halves convert exactly, two-sum normalises.
+__device__ __forceinline__ ff ff_from_ll(long long v, float pow2)
+{
+    const int vh = (int)(v >> 24);
+    const int vl = (int)(v & 0xffffff);
+    const ff s = fast_two_sum((float)vh * 16777216.0f, (float)vl);
+    return {s.hi * pow2, s.lo * pow2};
+}
+constexpr float TWELFTH_HI = (float)(1.0 / 12.0);
+constexpr float TWELFTH_LO = (float)(1.0 / 12.0 - (double)(float)(1.0 / 12.0));
+// v * 2^-30 / 12 for an integer sum v of weighted rest-population differences.
+__device__ __forceinline__ ff ff_twelfth(long long v) { return ff_mul(ff_from_ll(v, FIX_INV), {TWELFTH_HI, TWELFTH_LO}); }
+
+// ---- pull sums --------------------------------------------------------------
+// The zeroth and first moments carry the exact integer sums (they feed the
+// float-float force balance); the second moments, which enter only through
+// the (1 - 1/tau) regularised part, are summed from h in FP32.
+struct PullSums {
+    float d, j0, j1, j2, sxx, syy, szz, sxy, sxz, syz;
+    long long Id, Ij0, Ij1, Ij2;
+};
+__device__ __forceinline__ void pull_zero(PullSums &p)
+{
+    p.d = p.j0 = p.j1 = p.j2 = p.sxx = p.syy = p.szz = p.sxy = p.sxz = p.syz = 0.f;
+    p.Id = p.Ij0 = p.Ij1 = p.Ij2 = 0;
+}
+// Adds direction i: g = g_i at the source (or the bounce-back value), d0 the
+// rest-population difference f_0(s) - f_0(x) in fixed point (0 at walls).
+__device__ __forceinline__ void pull_add(PullSums &p, int i, float g, int d0)
+{
+    const long long D = (long long)d0 * w12(i);
+    const float h = fmaf(w3(i) * FIX_INV, (float)d0, g);
+    p.d += g;
+    p.Id += D;
+    if (cx(i)) { p.j0 += cx(i) * g; p.sxx += h; p.Ij0 += cx(i) * D; }
+    if (cy(i)) { p.j1 += cy(i) * g; p.syy += h; p.Ij1 += cy(i) * D; }
+    if (cz(i)) { p.j2 += cz(i) * g; p.szz += h; p.Ij2 += cz(i) * D; }
+    if (cx(i) && cy(i)) p.sxy += cx(i) * cy(i) * h;
+    if (cx(i) && cz(i)) p.sxz += cx(i) * cz(i) * h;
+    if (cy(i) && cz(i)) p.syz += cy(i) * cz(i) * h;
+}
+
+// Moments of one component at one cell.
+struct CompMom {
+    float dr;          // rho - 3 f_0 (FP32)
+    ff rho;            // rho (float-float)
+    ff j[3];           // momentum of this component (float-float)
+    float S[6];        // sum c c h: xx, yy, zz, xy, xz, yz (FP32)
+    long long Ij[3];   // integer part of j, also gives grad(rho) below
+};
+__device__ __forceinline__ CompMom finish_moments(const PullSums &p, int f0)
+{
+    CompMom m;
+    const ff dff = ff_add_f(ff_twelfth(p.Id), p.d);
+    m.dr = dff.hi;
+    m.rho = ff_add(ff_from_ll(3LL * f0, FIX_INV), dff);
+    m.j[0] = ff_add_f(ff_twelfth(p.Ij0), p.j0);
+    m.j[1] = ff_add_f(ff_twelfth(p.Ij1), p.j1);
+    m.j[2] = ff_add_f(ff_twelfth(p.Ij2), p.j2);
+    m.Ij[0] = p.Ij0;
+    m.Ij[1] = p.Ij1;
+    m.Ij[2] = p.Ij2;
+    m.S[0] = p.sxx;
+    m.S[1] = p.syy;
+    m.S[2] = p.szz;
+    m.S[3] = p.sxy;
+    m.S[4] = p.sxz;
+    m.S[5] = p.syz;
+    return m;
+}
+
+// Accumulates the FP32 parts of grad(rho^a) (e = rho^a(x+c_i) - rho^a(x)
+// without the rest-population part) and, in gray cells, grad(At) with the
+// neighbour densities nA, nB.
+__device__ __forceinline__ void stencil_add(int i, float eA, float eB, float gf[2][3])
+{
+    const float wi = w3(i);
+    if (cx(i)) { gf[0][0] += wi * cx(i) * eA; gf[1][0] += wi * cx(i) * eB; }
+    if (cy(i)) { gf[0][1] += wi * cy(i) * eA; gf[1][1] += wi * cy(i) * eB; }
+    if (cz(i)) { gf[0][2] += wi * cz(i) * eA; gf[1][2] += wi * cz(i) * eB; }
+}
+__device__ __forceinline__ void atwood_add(int i, int w, float nA, float nB, float gAt[3])
+{
+    const float wi = w3(i);
+    const float nw = w == 0 ? nA : nB, nn = w == 0 ? nB : nA;
+    const float den = nw + nn;
+    const float At = den > 0.f ? (nw - nn) / den : 0.f;
+    if (cx(i)) gAt[0] += wi * cx(i) * At;
+    if (cy(i)) gAt[1] += wi * cy(i) * At;
+    if (cz(i)) gAt[2] += wi * cz(i) * At;
+}
+
+// Moment Hessian of a density: H = 9 M - 3 L I with M = sum_i w_i c_i c_i d_i
+// and L = sum_i w_i d_i, d_i = rho(x + c_i) - rho(x) (i.e. (1/cs^4) sum_i
+// w_i (c_i c_i - cs^2 I) d_i).  M is kept as xx, yy, zz, xy, xz, yz.
+struct HessSum {
+    float m[6], l;
+};
+__device__ __forceinline__ void hess_zero(HessSum &h)
+{
+    h.m[0] = h.m[1] = h.m[2] = h.m[3] = h.m[4] = h.m[5] = h.l = 0.f;
+}
+__device__ __forceinline__ void hess_add(HessSum &h, int i, float d)
+{
+    const float wd = wgt(i) * d;
+    h.l += wd;
+    if (cx(i)) h.m[0] += wd;
+    if (cy(i)) h.m[1] += wd;
+    if (cz(i)) h.m[2] += wd;
+    if (cx(i) && cy(i)) h.m[3] += cx(i) * cy(i) * wd;
+    if (cx(i) && cz(i)) h.m[4] += cx(i) * cz(i) * wd;
+    if (cy(i) && cz(i)) h.m[5] += cy(i) * cz(i) * wd;
+}
+// Divergence of the regularised normal g / s, s = sqrt(|g|^2 + eps^2):
+// tr(H)/s - g.H.g/s^3 (Eq. 4's curvature).
+__device__ __forceinline__ float normal_divergence(const float g[3], const HessSum &h, float eps)
+{
+    const float Hxx = 9.f * h.m[0] - 3.f * h.l, Hyy = 9.f * h.m[1] - 3.f * h.l, Hzz = 9.f * h.m[2] - 3.f * h.l;
+    const float Hxy = 9.f * h.m[3], Hxz = 9.f * h.m[4], Hyz = 9.f * h.m[5];
+    const float gHg = g[0] * (Hxx * g[0] + 2.f * (Hxy * g[1] + Hxz * g[2])) + g[1] * (Hyy * g[1] + 2.f * Hyz * g[2]) +
+                      g[2] * Hzz * g[2];
+    const float s2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2] + eps * eps;
+    const float s = sqrtf(s2);
+    return (Hxx + Hyy + Hzz) / s - gHg / (s2 * s);
+}
+
+// Forces, residual update, velocity and the regularised collision of one
+// fluid cell, then the store of the new state (and of the fields if MACRO).
+//   f0i  rest populations (fixed point) of the cell; M its moments;
+//   gf   FP32 parts of grad(rho^A), grad(rho^B); gAt grad(At) (gray cells);
+//   csf  whether Eq. 4 applies here; hA, hB the Hessian sums of rho^A, rho^B.
+//   tgt  tgt(i): offset within a component's array where direction i goes,
+//        i n + (index of x + c_i), or opp(i) n + c when x + c_i is solid.
+template <bool MACRO, class Target>
+__device__ __forceinline__ void collide_store(const DevParams &P, uint8_t t, int c, int n, const int f0i[2],
+                                              const CompMom M[2], const float gf[2][3], const float gAt[3],
+                                              bool csf, const HessSum &hA, const HessSum &hB,
+                                              GrayRec *__restrict__ gray,
+                                              float *__restrict__ fout, float *__restrict__ macro,
+                                              const Target &tgt)
+{
+    const float r[2] = {M[0].rho.hi, M[1].rho.hi};
+    const float rt = r[0] + r[1];
+    const bool is_gray = (t == CELL_GRAY);
+    const int w = P.wet;
+
+    // grad(rho^A), grad(rho^B) in float-float: the rest-population part is
+    // (1/4) 2^-30 sum_i w12_i c_i (f0(x+c_i) - f0(x)) = -2^-32 Ij
+    ff grA[3], grB[3];
+    float gA[3], gB[3];  // grad(phi^A) = grad(rho^B), grad(phi^B) = grad(rho^A)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        grA[d] = ff_add_f(ff_from_ll(-M[0].Ij[d], FIX_INV * 0.25f), gf[0][d]);
+        grB[d] = ff_add_f(ff_from_ll(-M[1].Ij[d], FIX_INV * 0.25f), gf[1][d]);
+        gA[d] = grB[d].hi;
+        gB[d] = grA[d].hi;
+    }
+    // Shan-Chen force in float-float: F^A = -G rho^A grad(rho^B), F^B = -G rho^B grad(rho^A)
+    const ff Gff = {P.G, P.G_lo};
+    ff Fsc[2][3];
+    float F[2][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        Fsc[0][d] = ff_mul(Gff, ff_mul(M[0].rho, grB[d]));
+        Fsc[1][d] = ff_mul(Gff, ff_mul(M[1].rho, grA[d]));
+        Fsc[0][d].hi = -Fsc[0][d].hi; Fsc[0][d].lo = -Fsc[0][d].lo;
+        Fsc[1][d].hi = -Fsc[1][d].hi; Fsc[1][d].lo = -Fsc[1][d].lo;
+        F[0][d] = r[0] * P.accel[0][d];  // the remaining (small) force terms, FP32
+        F[1][d] = r[1] * P.accel[1][d];
+    }
+    // CSF, Eq. 4: kappa (-div n^a) (grad phi^a / phi_avg) (rho^a / phi_max),
+    // phi^A = rho^B and phi^B = rho^A
+    if (csf) {
+        const float divA = normal_divergence(gA, hB, P.eps_n);
+        const float divB = normal_divergence(gB, hA, P.eps_n);
+        const float kA = P.kappa * (-divA) * r[0] * P.csf_coef[0];
+        const float kB = P.kappa * (-divB) * r[1] * P.csf_coef[1];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            F[0][d] += kA * gA[d];
+            F[1][d] += kB * gB[d];
+        }
+    }
+
+    // ---- residual state, saturation, Eq. 1 forces and velocity -------------
+    const float rw = r[w], rn = r[1 - w];
+    float s = (rw / rt - P.r_lo) * P.inv_r_span;
+    s = fminf(fmaxf(s, 0.f), 1.f);
+    float sw = s;
+    float u[3];
+    if (is_gray) {
+        const float4 ga = gray[c].a;
+        const float4 gb = gray[c].b;
+        unsigned meta = __float_as_uint(gb.w);
+        bool wetf = meta & META_WET;
+        bool swd = meta & META_SWITCHED;
+        bool changed = false;
+        if (wetf && s < P.s_lo) {
+            wetf = false; swd = true; changed = true;
+        } else if (!wetf && s > P.s_hi) {
+            wetf = true; swd = true; changed = true;
+        }
+        if (changed) {
+            meta = (meta & 0xffu) | (wetf ? META_WET : 0u) | META_SWITCHED;
+            reinterpret_cast<float *>(gray + c)[7] = __uint_as_float(meta);
+        }
+        const float Rw = (swd && !wetf) ? gb.y : 0.f;
+        const float Ro = (swd && wetf) ? gb.z : 0.f;
+        sw = Rw + (1.f - Rw - Ro) * s;
+        const Curve cv = P.curve[meta & 0xffu];
+
+        // capillary term of Eq. 1: -Pc(Sw) rho_r n H, H = |grad At|/2
+        const float At_c = (rw - rn) / (rw + rn);
+        const float mag = sqrtf(gAt[0] * gAt[0] + gAt[1] * gAt[1] + gAt[2] * gAt[2]);
+        const float H = (fabsf(At_c) <= P.at_cut) ? 0.5f * mag : 0.f;
+        if (H > 0.f) {
+            const float se_c = fminf(fmaxf((sw - cv.swr) * cv.inv_1m_swr, 1e-2f), 1.f);
+            const float Pc = gb.x * powf(se_c, cv.neg_inv_lambda);
+            const float k = -Pc * H / fmaxf(mag, P.eps_n);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                F[0][d] += k * (r[0] / rt) * gAt[d];
+                F[1][d] += k * (r[1] / rt) * gAt[d];
+            }
+        }
+        // viscous term of Eq. 1 with K^-1 = (1/K0)(I + v v^T) (Eq. 7)
+        const float se_k = fminf(fmaxf((sw - cv.swr) * cv.inv_1m_swr, 0.f), 1.f);
+        const float kr_w = powf(se_k, cv.nw), kr_n = powf(1.f - se_k, cv.nn);
+        const float coef = rw * P.nu[w] / fmaxf(kr_w, P.kr_min) + rn * P.nu[1 - w] / fmaxf(kr_n, P.kr_min);
+        const float rk = coef * ga.w;  // coef / K0
+        const float v[3] = {ga.x, ga.y, ga.z};
+        // (rho I + R/2) u = j + F/2 with R = rk (I + v v^T): Sherman-Morrison
+        float b[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            b[d] = ff_add_f(ff_add(ff_add(M[0].j[d], M[1].j[d]), ff_scale(ff_add(Fsc[0][d], Fsc[1][d]), 0.5f)),
+                            0.5f * (F[0][d] + F[1][d])).hi;
+        const float al = rt + 0.5f * rk, be = 0.5f * rk;
+        const float vb = v[0] * b[0] + v[1] * b[1] + v[2] * b[2];
+        const float vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        const float q = be * vb / (al + be * vv);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) u[d] = (b[d] - q * v[d]) / al;
+        const float vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float Ru = rk * (u[d] + v[d] * vu);
+            F[0][d] -= (r[0] / rt) * Ru;
+            F[1][d] -= (r[1] / rt) * Ru;
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            u[d] = ff_add_f(ff_add(ff_add(M[0].j[d], M[1].j[d]), ff_scale(ff_add(Fsc[0][d], Fsc[1][d]), 0.5f)),
+                            0.5f * (F[0][d] + F[1][d])).hi / rt;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        F[0][d] += Fsc[0][d].hi;
+        F[1][d] += Fsc[1][d].hi;
+    }
+
+    // ---- regularised collision, written as rest population + deviations ---
+    const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const float om = P.omega_fac[a];
+        const float ra = r[a];
+        const float *Fa = F[a];
+        const float *S = M[a].S;
+        const float uF = u[0] * Fa[0] + u[1] * Fa[1] + u[2] * Fa[2];
+        const float d3 = M[a].dr * (1.0f / 3.0f);
+        // Pi1 = sum c c h - (drho/3) I - rho u u + (uF + Fu)/2
+        const float Pxx = S[0] - d3 - ra * u[0] * u[0] + u[0] * Fa[0];
+        const float Pyy = S[1] - d3 - ra * u[1] * u[1] + u[1] * Fa[1];
+        const float Pzz = S[2] - d3 - ra * u[2] * u[2] + u[2] * Fa[2];
+        const float Pxy = S[3] - ra * u[0] * u[1] + 0.5f * (u[0] * Fa[1] + Fa[0] * u[1]);
+        const float Pxz = S[4] - ra * u[0] * u[2] + 0.5f * (u[0] * Fa[2] + Fa[0] * u[2]);
+        const float Pyz = S[5] - ra * u[1] * u[2] + 0.5f * (u[1] * Fa[2] + Fa[1] * u[2]);
+        const float trP = Pxx + Pyy + Pzz;
+        // f*_0 - f_0 = drho/3 - rho u^2/2 - om tr(Pi1)/2 - u.F/2, added exactly in
+        // fixed point; the sub-grid residual goes into the moving populations.
+        const float d0 = d3 - 0.5f * ra * uu - 0.5f * om * trP - 0.5f * uF;
+        const float xq = d0 * FIX_ONE;
+        const float qf = rintf(xq);
+        const float res = (xq - qf) * FIX_INV;
+        float *fo = fout + (size_t)a * Q * n;
+        reinterpret_cast<int *>(fo)[c] = f0i[a] + (int)qf;
+        // opposite pairs (i, i+1): cu, cF change sign, cPc does not, so
+        // g_i = E + O and g_{i+1} = E - O
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const float cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
+            const float cF = cx(i) * Fa[0] + cy(i) * Fa[1] + cz(i) * Fa[2];
+            float cPc = 0.f;
+            if (cx(i)) cPc += Pxx;
+            if (cy(i)) cPc += Pyy;
+            if (cz(i)) cPc += Pzz;
+            if (cx(i) && cy(i)) cPc += 2.0f * cx(i) * cy(i) * Pxy;
+            if (cx(i) && cz(i)) cPc += 2.0f * cx(i) * cz(i) * Pxz;
+            if (cy(i) && cz(i)) cPc += 2.0f * cy(i) * cz(i) * Pyz;
+            const float E = wgt(i) * (4.5f * ra * cu * cu + 4.5f * om * cPc + 4.5f * cu * cF + 3.0f * res);
+            const float O = wgt(i) * (3.0f * ra * cu + 1.5f * cF);
+            fo[tgt(i)] = E + O;
+            fo[tgt(i + 1)] = E - O;
+        }
+    }
+    if (MACRO) {
+        macro[c] = r[0];
+        macro[(size_t)n + c] = r[1];
+        macro[(size_t)2 * n + c] = u[0];
+        macro[(size_t)3 * n + c] = u[1];
+        macro[(size_t)4 * n + c] = u[2];
+        macro[(size_t)5 * n + c] = sw;
+    }
+}
+
+}  // namespace lbm

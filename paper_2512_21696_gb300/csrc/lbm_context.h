@@ -28,6 +28,8 @@ struct lbm_ctx {
     double *red = nullptr;             // reduction partials
     int red_blocks = 0;
 
+    int path = 0;   // 0: fused single launch, 1: two launches (density, collide)
+    int tile = 0;   // fused tile variant: 0 = 32x8, 1 = 32x16
     bool has_geometry = false;
     bool has_fields = false;
     long long steps = 0;
@@ -48,6 +50,7 @@ namespace lbm {
 cudaError_t launch_init(lbm_ctx *ctx, const float *rhoA, const float *rhoB, const float *u);
 cudaError_t launch_density(lbm_ctx *ctx);
 cudaError_t launch_collide(lbm_ctx *ctx, bool write_macro);
+cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro);
 cudaError_t launch_geometry(lbm_ctx *ctx, const uint8_t *ptype);
 cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16);
 cudaError_t launch_static_out(lbm_ctx *ctx, float *kinv6, float *pcs, float *swirr, float *sores);

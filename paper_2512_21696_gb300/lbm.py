@@ -20,7 +20,7 @@ __all__ = [
     "LbmError", "LbmContext", "lbm_default_params", "lbm_default_constitutive", "lbm_create",
     "lbm_destroy", "lbm_set_constitutive", "lbm_set_geometry", "lbm_init_fields", "lbm_step",
     "lbm_observables", "lbm_get_fields", "lbm_get_static", "lbm_save_state", "lbm_load_state",
-    "lbm_profile", "lbm_profile_read", "lbm_launch_count", "lbm_abi_version", "lbm_observables_noalloc",
+    "lbm_profile", "lbm_profile_read", "lbm_launch_count", "lbm_abi_version", "lbm_observables_noalloc", "lbm_set_kernel",
     "LBM_CELL_PORE", "LBM_CELL_SOLID", "LBM_CELL_GRAY", "LBM_STORAGE_F32", "LBM_STORAGE_F16S",
     "LBM_STORAGE_BF16S",
 ]
@@ -235,6 +235,11 @@ def lbm_profile_read(ctx: LbmContext) -> dict:
     cnt = C.c_int()
     _check(L.load().lbm_profile_read(ctx.handle, arr, 32, C.byref(cnt)), "lbm_profile_read")
     return {arr[k].name.decode(): (arr[k].launches, arr[k].total_ms) for k in range(min(cnt.value, 32))}
+
+
+def lbm_set_kernel(ctx: LbmContext, path: int = 0, tile: int = 0) -> None:
+    """Kernel path of lbm_step: 0 fused (default), 1 two launches; fused tile 0 = 32x8, 1 = 32x16."""
+    _check(L.load().lbm_set_kernel(ctx.handle, int(path), int(tile)), "lbm_set_kernel")
 
 
 def lbm_launch_count(ctx: LbmContext) -> int:

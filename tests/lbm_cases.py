@@ -77,11 +77,12 @@ def oracle_params(case: Case):
                          eps_n=s["eps_n"], kr_min=s["kr_min"], c_g=s["c_g"])
 
 
-def run_gpu(case: Case, steps: int, device_arrays=False, **extra):
+def run_gpu(case: Case, steps: int, device_arrays=False, path=0, tile=0, **extra):
     """Fields (rhoA, rhoB, u, sw), observables and static data after `steps`."""
     from paper_2512_21696_gb300 import lbm
     ctx = lbm.lbm_create(gpu_params(case, **extra))
     try:
+        lbm.lbm_set_kernel(ctx, path, tile)
         for k, cv in enumerate(case.curves):
             lbm.lbm_set_constitutive(ctx, k, lbm.lbm_default_constitutive(
                 kc_d=cv["kc_d"], pd=cv["pd"], lam=cv["lam"], swr=cv["swr"], nw=cv["nw"], nn=cv["nn"],

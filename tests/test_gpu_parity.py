@@ -41,10 +41,14 @@ def _compare_static(case, gstat, ostat):
     np.testing.assert_allclose(sores[gray], ostat["sores"][gray], rtol=2e-6, atol=1e-7)
 
 
+KERNELS = [(0, 0), (0, 1), (0, 2), (1, 0)]  # (path, tile): fused 32x8, 32x16, 32x8 x2, two launches
+
+
+@pytest.mark.parametrize("path,tile", KERNELS)
 @pytest.mark.parametrize("steps", [1, 10])
-def test_mixed_features_small(steps):
+def test_mixed_features_small(steps, path, tile):
     case = LC.mixed_features()
-    gf, gobs, gst = LC.run_gpu(case, steps)
+    gf, gobs, gst = LC.run_gpu(case, steps, path=path, tile=tile)
     of, oobs, ost = LC.run_oracle(case, steps)
     _compare_static(case, gst, ost)
     _compare(case, gf, of)
@@ -57,11 +61,13 @@ def test_mixed_features_device_arrays_and_tau():
     _compare(case, gf, of)
 
 
+@pytest.mark.parametrize("path,tile", KERNELS)
 @pytest.mark.parametrize("shape,periodic", [((5, 7, 13), (1, 1, 1)), ((9, 6, 11), (0, 1, 0)),
-                                            ((1, 17, 33), (1, 0, 1)), ((3, 3, 3), (0, 0, 0))])
-def test_ragged_and_open_boundaries(shape, periodic):
+                                            ((1, 17, 33), (1, 0, 1)), ((3, 3, 3), (0, 0, 0)),
+                                            ((20, 37, 70), (1, 1, 0))])
+def test_ragged_and_open_boundaries(shape, periodic, path, tile):
     case = LC.mixed_features(shape=shape, periodic=periodic, seed=sum(shape))
-    gf, _, gst = LC.run_gpu(case, 12)
+    gf, _, gst = LC.run_gpu(case, 12, path=path, tile=tile)
     of, _, ost = LC.run_oracle(case, 12)
     _compare_static(case, gst, ost)
     _compare(case, gf, of)
@@ -197,3 +203,13 @@ def test_mass_conservation_fp32():
     gf, g1, _ = LC.run_gpu(case, 300)
     for a in range(2):
         assert abs(g1["mass"][a] - g0["mass"][a]) < 2e-6 * g0["mass"][a]
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2])
+def test_fused_matches_two_launch_path(tile):
+    """The fused kernel and the two-launch path share the per-cell arithmetic."""
+    case = LC.drainage(48)
+    a, _, _ = LC.run_gpu(case, 25, path=0, tile=tile)
+    b, _, _ = LC.run_gpu(case, 25, path=1)
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(x, y, rtol=0, atol=2e-6 * max(1.0, np.abs(y).max()))
