@@ -186,8 +186,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t_wall0 = time.time()
     ev0.record(stream)
-    for _ in range(args.steps):
-        lbm.lbm_step(ctx, 1)
+    lbm.lbm_step(ctx, args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     t_wall1 = time.time()
@@ -338,7 +337,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", type=int, default=0, help="0 fused single launch, 1 two launches")
-    ap.add_argument("--tile", type=int, default=0, help="fused tile: 0 = 32x8, 1 = 32x16")
+    ap.add_argument("--tile", type=int, default=2,
+                    help="fused tile: 0 = 32x8, 1 = 32x16, 2 = 32x8 two CTAs/SM, 3 = 32x12, 4 = 64x8")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -232,8 +232,8 @@ LBM_API int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *c
 /* Kernel path of lbm_step: path 0 (default) = one fused launch per step
  * (rolling z-window with shared-memory halos), path 1 = two launches
  * (densities, then forces + collision).  tile selects the fused tile:
- * 0 = 32x8 columns, 1 = 32x16, 2 = 32x8 with two CTAs per SM.  Both paths
- * compute identical states.
+ * 0 = 32x8 columns, 1 = 32x16, 2 = 32x8 with two CTAs per SM (the default),
+ * 3 = 32x12, 4 = 64x8.  Both paths and all tiles compute identical states.
  * LBM_ERR_ARG on unknown values. */
 LBM_API int lbm_set_kernel(lbm_ctx *ctx, int path, int tile);
 

@@ -90,6 +90,10 @@ void fill_device_params(lbm_ctx *ctx)
     d.at_cut = (float)p.at_cut;
     d.eps_n = (float)p.eps_n;
     d.kr_min = (float)p.kr_min;
+    {
+        const double ww = p.rho_wall[p.wet_idx], wn = p.rho_wall[1 - p.wet_idx];
+        d.at_wall = ww + wn > 0 ? (float)((ww - wn) / (ww + wn)) : 0.0f;
+    }
     for (int k = 0; k < LBM_MAX_PORE_TYPES; ++k) {
         const lbm_constitutive &c = ctx->curves[k];
         d.curve[k].swr = (float)c.swr;
@@ -254,7 +258,7 @@ int lbm_create(lbm_ctx **out, const lbm_params *p)
     if (e == cudaSuccess) e = cudaMalloc(&ctx->type, N);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->phi, N * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->gray, N * sizeof(lbm::GrayRec));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->rho, 2 * N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->rho, 3 * N * sizeof(float));  // drho^A, drho^B, At
     if (e == cudaSuccess) e = cudaMalloc(&ctx->macro, 6 * N * sizeof(float));
     ctx->red_blocks = lbm::obs_blocks(ctx->n);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->red, (size_t)(ctx->red_blocks + 1) * lbm::NOBS_HOST * sizeof(double));
@@ -547,7 +551,7 @@ int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *count)
 
 int lbm_set_kernel(lbm_ctx *ctx, int path, int tile)
 {
-    if (!ctx || path < 0 || path > 1 || tile < 0 || tile > 2) return LBM_ERR_ARG;
+    if (!ctx || path < 0 || path > 1 || tile < 0 || tile > 4) return LBM_ERR_ARG;
     ctx->path = path;
     ctx->tile = tile;
     return LBM_OK;

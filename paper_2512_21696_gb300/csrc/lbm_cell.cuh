@@ -150,12 +150,19 @@ __device__ __forceinline__ void stencil_add(int i, float eA, float eB, float gf[
     if (cy(i)) { gf[0][1] += wi * cy(i) * eA; gf[1][1] += wi * cy(i) * eB; }
     if (cz(i)) { gf[0][2] += wi * cz(i) * eA; gf[1][2] += wi * cz(i) * eB; }
 }
-__device__ __forceinline__ void atwood_add(int i, int w, float nA, float nB, float gAt[3])
+// Atwood number At = (rho^w - rho^n)/(rho^w + rho^n) of a fluid cell from its
+// fixed-point rest populations and drho; evaluated once per cell and step
+// (approximate division, 2 ulp) and read by the gray-cell stencils.
+__device__ __forceinline__ float atwood_of(int w, int f0A, int f0B, float drA, float drB)
+{
+    const float rA = fmaf((float)f0A, 3.0f * FIX_INV, drA), rB = fmaf((float)f0B, 3.0f * FIX_INV, drB);
+    const float nw = w == 0 ? rA : rB, nn = w == 0 ? rB : rA;
+    const float den = nw + nn;
+    return den > 0.f ? __fdividef(nw - nn, den) : 0.f;
+}
+__device__ __forceinline__ void atwood_add(int i, float At, float gAt[3])
 {
     const float wi = w3(i);
-    const float nw = w == 0 ? nA : nB, nn = w == 0 ? nB : nA;
-    const float den = nw + nn;
-    const float At = den > 0.f ? (nw - nn) / den : 0.f;
     if (cx(i)) gAt[0] += wi * cx(i) * At;
     if (cy(i)) gAt[1] += wi * cy(i) * At;
     if (cz(i)) gAt[2] += wi * cz(i) * At;
@@ -191,8 +198,8 @@ __device__ __forceinline__ float normal_divergence(const float g[3], const HessS
     const float gHg = g[0] * (Hxx * g[0] + 2.f * (Hxy * g[1] + Hxz * g[2])) + g[1] * (Hyy * g[1] + 2.f * Hyz * g[2]) +
                       g[2] * Hzz * g[2];
     const float s2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2] + eps * eps;
-    const float s = sqrtf(s2);
-    return (Hxx + Hyy + Hzz) / s - gHg / (s2 * s);
+    const float is = rsqrtf(s2);
+    return is * ((Hxx + Hyy + Hzz) - gHg * is * is);
 }
 
 // Forces, residual update, velocity and the regularised collision of one
@@ -239,6 +246,15 @@ __device__ __forceinline__ void collide_store(const DevParams &P, uint8_t t, int
         F[0][d] = r[0] * P.accel[0][d];  // the remaining (small) force terms, FP32
         F[1][d] = r[1] * P.accel[1][d];
     }
+    // the cancelling part of the momentum balance, j + F_sc/2, in float-float;
+    // the remaining forces are added to it in FP32 below
+    ff Bmix[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        Bmix[d] = ff_add(ff_add(M[0].j[d], M[1].j[d]), ff_scale(ff_add(Fsc[0][d], Fsc[1][d]), 0.5f));
+    }
+    const float FscA[3] = {Fsc[0][0].hi, Fsc[0][1].hi, Fsc[0][2].hi};
+    const float FscB[3] = {Fsc[1][0].hi, Fsc[1][1].hi, Fsc[1][2].hi};
     // CSF, Eq. 4: kappa (-div n^a) (grad phi^a / phi_avg) (rho^a / phi_max),
     // phi^A = rho^B and phi^B = rho^A
     if (csf) {
@@ -280,55 +296,57 @@ __device__ __forceinline__ void collide_store(const DevParams &P, uint8_t t, int
         sw = Rw + (1.f - Rw - Ro) * s;
         const Curve cv = P.curve[meta & 0xffu];
 
-        // capillary term of Eq. 1: -Pc(Sw) rho_r n H, H = |grad At|/2
-        const float At_c = (rw - rn) / (rw + rn);
+        // capillary term of Eq. 1: -Pc(Sw) rho_r n H, H = |grad At|/2.  The
+        // gray-cell terms are smooth coefficients of the balance, evaluated
+        // with approximate division and the exp2/log2 power (a few ulp).
+        const float irt = __fdividef(1.0f, rt);
+        const float At_c = __fdividef(rw - rn, rw + rn);
         const float mag = sqrtf(gAt[0] * gAt[0] + gAt[1] * gAt[1] + gAt[2] * gAt[2]);
         const float H = (fabsf(At_c) <= P.at_cut) ? 0.5f * mag : 0.f;
         if (H > 0.f) {
             const float se_c = fminf(fmaxf((sw - cv.swr) * cv.inv_1m_swr, 1e-2f), 1.f);
-            const float Pc = gb.x * powf(se_c, cv.neg_inv_lambda);
-            const float k = -Pc * H / fmaxf(mag, P.eps_n);
+            const float Pc = gb.x * __powf(se_c, cv.neg_inv_lambda);
+            const float k = __fdividef(-Pc * H, fmaxf(mag, P.eps_n)) * irt;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                F[0][d] += k * (r[0] / rt) * gAt[d];
-                F[1][d] += k * (r[1] / rt) * gAt[d];
+                F[0][d] += k * r[0] * gAt[d];
+                F[1][d] += k * r[1] * gAt[d];
             }
         }
         // viscous term of Eq. 1 with K^-1 = (1/K0)(I + v v^T) (Eq. 7)
         const float se_k = fminf(fmaxf((sw - cv.swr) * cv.inv_1m_swr, 0.f), 1.f);
-        const float kr_w = powf(se_k, cv.nw), kr_n = powf(1.f - se_k, cv.nn);
-        const float coef = rw * P.nu[w] / fmaxf(kr_w, P.kr_min) + rn * P.nu[1 - w] / fmaxf(kr_n, P.kr_min);
+        const float kr_w = se_k > 0.f ? __powf(se_k, cv.nw) : 0.f;
+        const float kr_n = se_k < 1.f ? __powf(1.f - se_k, cv.nn) : 0.f;
+        const float coef = __fdividef(rw * P.nu[w], fmaxf(kr_w, P.kr_min)) +
+                           __fdividef(rn * P.nu[1 - w], fmaxf(kr_n, P.kr_min));
         const float rk = coef * ga.w;  // coef / K0
         const float v[3] = {ga.x, ga.y, ga.z};
         // (rho I + R/2) u = j + F/2 with R = rk (I + v v^T): Sherman-Morrison
         float b[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-            b[d] = ff_add_f(ff_add(ff_add(M[0].j[d], M[1].j[d]), ff_scale(ff_add(Fsc[0][d], Fsc[1][d]), 0.5f)),
-                            0.5f * (F[0][d] + F[1][d])).hi;
+        for (int d = 0; d < 3; ++d) b[d] = ff_add_f(Bmix[d], 0.5f * (F[0][d] + F[1][d])).hi;
         const float al = rt + 0.5f * rk, be = 0.5f * rk;
         const float vb = v[0] * b[0] + v[1] * b[1] + v[2] * b[2];
         const float vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-        const float q = be * vb / (al + be * vv);
+        const float q = __fdividef(be * vb, al + be * vv);
+        const float ial = __fdividef(1.0f, al);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) u[d] = (b[d] - q * v[d]) / al;
+        for (int d = 0; d < 3; ++d) u[d] = (b[d] - q * v[d]) * ial;
         const float vu = v[0] * u[0] + v[1] * u[1] + v[2] * u[2];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const float Ru = rk * (u[d] + v[d] * vu);
-            F[0][d] -= (r[0] / rt) * Ru;
-            F[1][d] -= (r[1] / rt) * Ru;
+            const float Ru = rk * (u[d] + v[d] * vu) * irt;
+            F[0][d] -= r[0] * Ru;
+            F[1][d] -= r[1] * Ru;
         }
     } else {
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-            u[d] = ff_add_f(ff_add(ff_add(M[0].j[d], M[1].j[d]), ff_scale(ff_add(Fsc[0][d], Fsc[1][d]), 0.5f)),
-                            0.5f * (F[0][d] + F[1][d])).hi / rt;
+        for (int d = 0; d < 3; ++d) u[d] = ff_add_f(Bmix[d], 0.5f * (F[0][d] + F[1][d])).hi / rt;
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        F[0][d] += Fsc[0][d].hi;
-        F[1][d] += Fsc[1][d].hi;
+        F[0][d] += FscA[d];
+        F[1][d] += FscB[d];
     }
 
     // ---- regularised collision, written as rest population + deviations ---

@@ -64,6 +64,7 @@ struct DevParams {
     int wet;
     float r_lo, inv_r_span;
     float s_lo, s_hi, at_cut, eps_n, kr_min;
+    float at_wall;         // Atwood number of the wall densities
     Curve curve[MAX_TYPES];
 };
 

@@ -29,7 +29,7 @@ struct lbm_ctx {
     int red_blocks = 0;
 
     int path = 0;   // 0: fused single launch, 1: two launches (density, collide)
-    int tile = 0;   // fused tile variant: 0 = 32x8, 1 = 32x16
+    int tile = 2;   // fused tile variant (lbm_set_kernel); 2 = 32x8, two CTAs per SM
     bool has_geometry = false;
     bool has_fields = false;
     long long steps = 0;

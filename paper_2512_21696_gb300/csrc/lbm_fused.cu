@@ -42,7 +42,10 @@ struct Tiles {
     static constexpr int NT = TX * TY;
     static constexpr int RX = TX + 4, RY = TY + 4, RN = RX * RY;
     static constexpr int DX = TX + 2, DY = TY + 2, DN = DX * DY;
-    static constexpr size_t smem() { return 3 * RN * sizeof(RawCell) + 3 * DN * (sizeof(DenCell) + sizeof(DenMeta)); }
+    static constexpr size_t smem()
+    {
+        return 3 * RN * sizeof(RawCell) + 3 * DN * (sizeof(DenCell) + sizeof(DenMeta) + sizeof(float));
+    }
 };
 
 __device__ __forceinline__ int wrap_coord(int v, int n, int per)
@@ -64,6 +67,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
     RawCell *raw = reinterpret_cast<RawCell *>(smem_raw);         // [3][RN]
     DenCell *den = reinterpret_cast<DenCell *>(raw + 3 * T::RN);  // [3][DN]
     DenMeta *dmeta = reinterpret_cast<DenMeta *>(den + 3 * T::DN); // [3][DN]
+    float *dat = reinterpret_cast<float *>(dmeta + 3 * T::DN);     // [3][DN] Atwood number
 
     const int n = P.n;
     const int tid = threadIdx.x;
@@ -107,6 +111,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
             const RawCell *r2 = raw + ring3(L + 1) * T::RN;
             DenCell *dd = den + ring3(L) * T::DN;
             DenMeta *dm = dmeta + ring3(L) * T::DN;
+            float *da = dat + ring3(L) * T::DN;
             const int gz = wrap_coord(L, P.nz, P.per[2]);
             for (int e = tid; e < T::DN; e += T::NT) {
                 const int dx = e % T::DX, dy = e / T::DX;
@@ -136,6 +141,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                 }
                 dd[e] = dc;
                 dm[e] = {me.type, g};
+                da[e] = me.type != CELL_SOLID ? atwood_of(P.wet, dc.f0A, dc.f0B, dc.drA, dc.drB) : P.at_wall;
             }
         };
 
@@ -149,6 +155,9 @@ __global__ void __launch_bounds__(TX *TY, MINB)
             const DenMeta *m0 = dmeta + ring3(z - 1) * T::DN;
             const DenMeta *m1 = dmeta + ring3(z) * T::DN;
             const DenMeta *m2 = dmeta + ring3(z + 1) * T::DN;
+            const float *a0 = dat + ring3(z - 1) * T::DN;
+            const float *a1 = dat + ring3(z) * T::DN;
+            const float *a2 = dat + ring3(z + 1) * T::DN;
             const int dk = (ux + 1) + T::DX * (uy + 1);
             const DenMeta me = m1[dk];
             if (me.type == CELL_SOLID) {
@@ -200,15 +209,12 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                 const float eA = wl ? P.rho_wall[0] - r[0] : nd.drA - dc.drA;
                 const float eB = wl ? P.rho_wall[1] - r[1] : nd.drB - dc.drB;
                 stencil_add(i, eA, eB, gf);
-                if (is_gray || csf) {
+                if (is_gray) atwood_add(i, (cz(i) < 0 ? a0 : (cz(i) > 0 ? a2 : a1))[dk + cx(i) + T::DX * cy(i)], gAt);
+                if (csf) {
                     const float dA = wl ? eA : 3.0f * fix_diff(nd.f0A, f0i[0]) + eA;
                     const float dB = wl ? eB : 3.0f * fix_diff(nd.f0B, f0i[1]) + eB;
-                    if (is_gray)
-                        atwood_add(i, P.wet, wl ? P.rho_wall[0] : r[0] + dA, wl ? P.rho_wall[1] : r[1] + dB, gAt);
-                    if (csf) {
-                        hess_add(hA, i, dA);
-                        hess_add(hB, i, dB);
-                    }
+                    hess_add(hA, i, dA);
+                    hess_add(hB, i, dB);
                 }
             }
             auto tgt = [&](int i) -> size_t {
@@ -274,13 +280,16 @@ static cudaError_t launch_fused_tile(lbm_ctx *ctx, bool write_macro)
     return write_macro ? launch_fused_t<TX, TY, MINB, true>(ctx) : launch_fused_t<TX, TY, MINB, false>(ctx);
 }
 
-// Tile variants: 0 = 32x8 (one CTA per SM, no register cap), 1 = 32x16,
-// 2 = 32x8 with two CTAs per SM (128 registers).
+// Tile variants: 0 = 32x8 (one CTA per SM, no register cap), 1 = 32x16
+// (128 registers), 2 = 32x8 with two CTAs per SM (128 registers), 3 = 32x12
+// (168 registers), 4 = 64x8 (128 registers).
 cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro)
 {
     switch (ctx->tile) {
     case 1: return launch_fused_tile<32, 16, 1>(ctx, write_macro);
     case 2: return launch_fused_tile<32, 8, 2>(ctx, write_macro);
+    case 3: return launch_fused_tile<32, 12, 1>(ctx, write_macro);
+    case 4: return launch_fused_tile<64, 8, 1>(ctx, write_macro);
     default: return launch_fused_tile<32, 8, 1>(ctx, write_macro);
     }
 }

@@ -70,6 +70,7 @@ __global__ void k_init(DevParams P, const float *__restrict__ rhoA, const float 
         for (int k = 0; k < 2 * Q; ++k) f[(size_t)k * n + c] = 0.0f;
         drho[c] = 0.0f;
         drho[n + c] = 0.0f;
+        drho[(size_t)2 * n + c] = P.at_wall;
         for (int k = 0; k < 6; ++k) macro[(size_t)k * n + c] = 0.0f;
         return;
     }
@@ -154,6 +155,8 @@ __global__ void __launch_bounds__(256) k_density(DevParams P, const float *__res
         }
         drho[(size_t)a * n + c] = ff_add_f(ff_twelfth(id), acc).hi;
     }
+    drho[(size_t)2 * n + c] = atwood_of(P.wet, reinterpret_cast<const int *>(f)[c],
+                                        reinterpret_cast<const int *>(f + (size_t)Q * n)[c], drho[c], drho[n + c]);
 }
 
 // ---------------------------------------------------------------------------
@@ -227,15 +230,12 @@ __global__ void __launch_bounds__(256) k_collide(DevParams P, const float *__res
         const float eA = wl ? P.rho_wall[0] - r[0] : drA[m] - drcA;
         const float eB = wl ? P.rho_wall[1] - r[1] : drB[m] - drcB;
         stencil_add(i, eA, eB, gf);
-        if (is_gray || csf) {
+        if (is_gray) atwood_add(i, wl ? P.at_wall : drho[(size_t)2 * n + m], gAt);
+        if (csf) {
             const float dA = wl ? eA : 3.0f * fix_diff(fiA[m], f0i[0]) + eA;
             const float dB = wl ? eB : 3.0f * fix_diff(fiB[m], f0i[1]) + eB;
-            if (is_gray)
-                atwood_add(i, P.wet, wl ? P.rho_wall[0] : r[0] + dA, wl ? P.rho_wall[1] : r[1] + dB, gAt);
-            if (csf) {
-                hess_add(hA, i, dA);
-                hess_add(hB, i, dB);
-            }
+            hess_add(hA, i, dA);
+            hess_add(hB, i, dB);
         }
     }
     auto tgt = [&](int i) -> size_t {

@@ -41,7 +41,7 @@ def _compare_static(case, gstat, ostat):
     np.testing.assert_allclose(sores[gray], ostat["sores"][gray], rtol=2e-6, atol=1e-7)
 
 
-KERNELS = [(0, 0), (0, 1), (0, 2), (1, 0)]  # (path, tile): fused 32x8, 32x16, 32x8 x2, two launches
+KERNELS = [(0, 0), (0, 1), (0, 2), (0, 3), (0, 4), (1, 0)]  # (path, tile): fused tiles 0-4, two launches
 
 
 @pytest.mark.parametrize("path,tile", KERNELS)
@@ -205,7 +205,7 @@ def test_mass_conservation_fp32():
         assert abs(g1["mass"][a] - g0["mass"][a]) < 2e-6 * g0["mass"][a]
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
 def test_fused_matches_two_launch_path(tile):
     """The fused kernel and the two-launch path share the per-cell arithmetic."""
     case = LC.drainage(48)
