@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & HBM-roofline % of 2-comp D3Q19 step; mixed/adjoint/batched vs plain FP32"
+STORAGE_IDS = {"f32": 0, "f16": 1, "bf16": 2, "f16r": 3, "bf16r": 4}
 WORKLOAD = "drainage in synthetic multiscale rock, 128^3, 2-component D3Q19, FP32"
 EDGE = 128
 FALLBACK_HBM_GBS = 6800.0
@@ -56,7 +57,10 @@ def algorithmic_bytes(cell):
     gray = int((cell == 2).sum())
     step = fluid * 304 + n * 1 + gray * 25
     return dict(step=step,
+                step_lp=fluid * 152 + n * 1 + gray * 25,
+                step_r16=fluid * 160 + n * 1 + gray * 25,
                 k_fused=fluid * 304 + n * 1 + gray * 32,
+                k_fused_lp=fluid * 152 + n * 1 + gray * 32,
                 k_collide=fluid * 304 + n * 1 + n * 8 + gray * 32,
                 k_density=fluid * 152 + n * 1 + n * 8), fluid, gray
 
@@ -164,7 +168,7 @@ def run_ours(args, rank, world, local_rank):
     nz, ny, nx = cell.shape
     n = cell.size
     stream = torch.cuda.current_stream()
-    p = lbm.lbm_default_params(nx, ny, nz, stream=stream.cuda_stream, **SETTINGS)
+    p = lbm.lbm_default_params(nx, ny, nz, stream=stream.cuda_stream, storage=STORAGE_IDS[args.storage], **SETTINGS)
     ctx = lbm.lbm_create(p)
     lbm.lbm_set_kernel(ctx, args.path, args.tile)
     lbm.lbm_set_constitutive(ctx, 0, lbm.lbm_default_constitutive())
@@ -233,24 +237,27 @@ def run_ours(args, rank, world, local_rank):
     dname, (dlaunch, dtotal) = dom
     avg_s = dtotal / max(dlaunch, 1) * 1e-3
     peak, peak_kind = measured_peak()
-    achieved = alg.get(dname, alg["step"]) / avg_s / 1e9
-    step_gbs = alg["step"] * args.steps / (ms * 1e-3) / 1e9
+    step_key = {"f32": "step", "f16": "step_lp", "bf16": "step_lp"}.get(args.storage, "step_r16")
+    dkey = dname if args.storage in ("f32", "f16", "bf16") else "step_r16"
+    achieved = alg.get(dkey, alg[step_key]) / avg_s / 1e9
+    step_gbs = alg[step_key] * args.steps / (ms * 1e-3) / 1e9
     h2d = 2 * n * 4
     d2h = 6 * n * 4 + 128
     out = {
         "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded multiscale-rock recipe)",
-        "config": {"workload": WORKLOAD, "cells": n, "fluid_frac": round(fluid / n, 4),
+        "config": {"workload": WORKLOAD if args.storage == "f32" else WORKLOAD.replace("FP32", f"{args.storage.upper()} shifted storage, FP32 arithmetic"),
+                   "storage": args.storage, "cells": n, "fluid_frac": round(fluid / n, 4),
                    "gray_frac": round(gray / n, 4), "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (2 x 319 MB population buffers)",
                    "kernels_per_step": round(launches / args.steps, 3)},
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": ncu_traffic(dname),
-                     "alg_bytes_per_launch": alg.get(dname, alg["step"]),
+                     "alg_bytes_per_launch": alg.get(dkey, alg[step_key]),
                      "avg_launch_ms": round(avg_s * 1e3, 5)},
-        "step_roofline": {"alg_bytes_per_cell": round(alg["step"] / n, 2), "achieved_gbs": round(step_gbs, 1),
+        "step_roofline": {"alg_bytes_per_cell": round(alg[step_key] / n, 2), "achieved_gbs": round(step_gbs, 1),
                           "frac": round(step_gbs / peak, 4)},
         "kernels": {k: {"launches": v[0], "avg_ms": round(v[1] / max(v[0], 1), 5)} for k, v in prof.items()},
         "e2e": {"value": round(world * n * args.steps / (e_ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
@@ -337,6 +344,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", type=int, default=0, help="0 fused single launch, 1 two launches")
+    ap.add_argument("--storage", choices=list(STORAGE_IDS), default="f32",
+                    help="population storage: f32; f16 / bf16 globally shifted; f16r / bf16r rest-referenced (FP32 arithmetic)")
     ap.add_argument("--tile", type=int, default=2,
                     help="fused tile: 0 = 32x8, 1 = 32x16, 2 = 32x8 two CTAs/SM, 3 = 32x12, 4 = 64x8")
     args = ap.parse_args()

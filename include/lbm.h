@@ -73,9 +73,21 @@ enum lbm_cell { LBM_CELL_PORE = 0, LBM_CELL_SOLID = 1, LBM_CELL_GRAY = 2 };
 
 /* Population storage.  F32: the rest population f_0 and the deviations
  * f_i - 3 w_i f_0 (i >= 1) of each cell, in FP32.  F16S / BF16S: the shifted
- * deviations f_i - w_i rho0 (rho0 = (rho_hi + rho_lo)/2) in FP16 / BF16.
- * All storages compute in FP32. */
-enum lbm_storage { LBM_STORAGE_F32 = 0, LBM_STORAGE_F16S = 1, LBM_STORAGE_BF16S = 2 };
+ * deviations f_i - w_i rho0 (rho0 = (rho_hi + rho_lo)/2, i = 0..18) in
+ * FP16 / BF16, half the bytes per cell.  All storages compute in FP32; the
+ * 16-bit storages always run the fused one-launch kernel (lbm_set_kernel's
+ * path choice applies to F32) and their checkpoints hold 16-bit slots.
+ * F16R / BF16R: the F32 layout's rest population (int32) with the 18
+ * deviations f_i - 3 w_i f_0(source) in FP16 (scaled by 2^12) / BF16: the
+ * stored numbers are only the velocity and non-equilibrium parts, 80 bytes
+ * per cell, fused kernel with the default tile. */
+enum lbm_storage {
+    LBM_STORAGE_F32 = 0,
+    LBM_STORAGE_F16S = 1,
+    LBM_STORAGE_BF16S = 2,
+    LBM_STORAGE_F16R = 3,
+    LBM_STORAGE_BF16R = 4
+};
 
 /* Model and run parameters.  Index 0 is component A, 1 is component B. */
 typedef struct lbm_params {

@@ -61,6 +61,18 @@ bool valid_curve(const lbm_constitutive &c)
            std::isfinite(c.aniso);
 }
 
+// Bytes of one population buffer: 2 components x 19 slots x n cells.
+size_t pop_bytes(const lbm_ctx *ctx)
+{
+    const size_t n = (size_t)ctx->n;
+    switch (ctx->p.storage) {
+    case LBM_STORAGE_F32: return 2 * lbm::Q * n * sizeof(float);
+    case LBM_STORAGE_F16R:
+    case LBM_STORAGE_BF16R: return 2 * n * sizeof(int) + 2 * (lbm::Q - 1) * n * sizeof(uint16_t);
+    default: return 2 * lbm::Q * n * sizeof(uint16_t);
+    }
+}
+
 void fill_device_params(lbm_ctx *ctx)
 {
     const lbm_params &p = ctx->p;
@@ -90,6 +102,8 @@ void fill_device_params(lbm_ctx *ctx)
     d.at_cut = (float)p.at_cut;
     d.eps_n = (float)p.eps_n;
     d.kr_min = (float)p.kr_min;
+    d.rho0[0] = d.rho0[1] = (float)(0.5 * (p.rho_hi + p.rho_lo));
+    d.storage = p.storage;
     {
         const double ww = p.rho_wall[p.wet_idx], wn = p.rho_wall[1 - p.wet_idx];
         d.at_wall = ww + wn > 0 ? (float)((ww - wn) / (ww + wn)) : 0.0f;
@@ -236,7 +250,7 @@ int lbm_create(lbm_ctx **out, const lbm_params *p)
     if (p->wet_idx != 0 && p->wet_idx != 1) return LBM_ERR_ARG;
     if (!(p->s_lo >= 0 && p->s_lo < p->s_hi && p->s_hi <= 1)) return LBM_ERR_ARG;
     if (!(p->eps_n > 0 && p->kr_min > 0 && p->at_cut >= 0 && p->c_g >= 0)) return LBM_ERR_ARG;
-    if (p->storage != LBM_STORAGE_F32) return LBM_ERR_ARG;
+    if (p->storage < LBM_STORAGE_F32 || p->storage > LBM_STORAGE_BF16R) return LBM_ERR_ARG;
     for (int a = 0; a < 2; ++a)
         for (int k = 0; k < 3; ++k)
             if (!std::isfinite(p->body_accel[a][k])) return LBM_ERR_ARG;
@@ -254,7 +268,7 @@ int lbm_create(lbm_ctx **out, const lbm_params *p)
     fill_device_params(ctx);
     const size_t N = (size_t)n;
     cudaError_t e = cudaSuccess;
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&ctx->f[b], 2 * lbm::Q * N * sizeof(float));
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&ctx->f[b], pop_bytes(ctx));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->type, N);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->phi, N * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->gray, N * sizeof(lbm::GrayRec));
@@ -376,7 +390,9 @@ int lbm_step(lbm_ctx *ctx, int nsteps)
     DeviceGuard g(ctx->dev);
     if (!g.ok) return LBM_ERR_CUDA;
     for (int k = 0; k < nsteps; ++k) {
-        if (ctx->path == 1) {
+        if (ctx->p.storage == LBM_STORAGE_F16S || ctx->p.storage == LBM_STORAGE_BF16S) {
+            LBM_CUDA(lbm::launch_fused_lp(ctx, k == nsteps - 1));
+        } else if (ctx->path == 1 && ctx->p.storage == LBM_STORAGE_F32) {
             LBM_CUDA(lbm::launch_density(ctx));
             LBM_CUDA(lbm::launch_collide(ctx, k == nsteps - 1));
         } else {
@@ -449,12 +465,12 @@ int lbm_get_static(lbm_ctx *ctx, float *kinv, float *pc_scale, float *sw_irr, fl
     return LBM_OK;
 }
 
-// Checkpoint layout: [int64 magic][int64 n][int64 steps][int64 cur]
-// [populations 38 n float][gray records n * 32 B][macro 6 n float].
+// Checkpoint layout: [int64 magic][int64 n][int64 steps][int64 storage]
+// [populations 38 n slots of the storage][gray records n * 32 B][macro 6 n float].
 static size_t state_bytes(const lbm_ctx *ctx)
 {
     const size_t N = (size_t)ctx->n;
-    return 4 * sizeof(long long) + 2 * lbm::Q * N * sizeof(float) + N * sizeof(lbm::GrayRec) + 6 * N * sizeof(float);
+    return 4 * sizeof(long long) + pop_bytes(ctx) + N * sizeof(lbm::GrayRec) + 6 * N * sizeof(float);
 }
 static const long long STATE_MAGIC = 0x4c424d3253544154LL;  // "LBM2STAT"
 
@@ -476,10 +492,10 @@ int lbm_save_state(lbm_ctx *ctx, void *buf, size_t bytes)
     hdr[0] = STATE_MAGIC;
     hdr[1] = ctx->n;
     hdr[2] = ctx->steps;
-    hdr[3] = 0;
+    hdr[3] = ctx->p.storage;
     char *p = (char *)buf + 4 * sizeof(long long);
-    LBM_CUDA(cudaMemcpyAsync(p, ctx->f[ctx->cur], 2 * lbm::Q * N * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
-    p += 2 * lbm::Q * N * sizeof(float);
+    LBM_CUDA(cudaMemcpyAsync(p, ctx->f[ctx->cur], pop_bytes(ctx), cudaMemcpyDeviceToHost, ctx->stream));
+    p += pop_bytes(ctx);
     LBM_CUDA(cudaMemcpyAsync(p, ctx->gray, N * sizeof(lbm::GrayRec), cudaMemcpyDeviceToHost, ctx->stream));
     p += N * sizeof(lbm::GrayRec);
     LBM_CUDA(cudaMemcpyAsync(p, ctx->macro, 6 * N * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
@@ -492,14 +508,14 @@ int lbm_load_state(lbm_ctx *ctx, const void *buf, size_t bytes)
     if (!ctx || !buf || bytes < state_bytes(ctx)) return LBM_ERR_ARG;
     if (!ctx->has_geometry) return LBM_ERR_STATE;
     const long long *hdr = (const long long *)buf;
-    if (hdr[0] != STATE_MAGIC || hdr[1] != ctx->n) return LBM_ERR_ARG;
+    if (hdr[0] != STATE_MAGIC || hdr[1] != ctx->n || hdr[3] != ctx->p.storage) return LBM_ERR_ARG;
     DeviceGuard g(ctx->dev);
     if (!g.ok) return LBM_ERR_CUDA;
     const size_t N = (size_t)ctx->n;
     const char *p = (const char *)buf + 4 * sizeof(long long);
     ctx->cur = 0;
-    LBM_CUDA(cudaMemcpyAsync(ctx->f[0], p, 2 * lbm::Q * N * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    p += 2 * lbm::Q * N * sizeof(float);
+    LBM_CUDA(cudaMemcpyAsync(ctx->f[0], p, pop_bytes(ctx), cudaMemcpyHostToDevice, ctx->stream));
+    p += pop_bytes(ctx);
     LBM_CUDA(cudaMemcpyAsync(ctx->gray, p, N * sizeof(lbm::GrayRec), cudaMemcpyHostToDevice, ctx->stream));
     p += N * sizeof(lbm::GrayRec);
     LBM_CUDA(cudaMemcpyAsync(ctx->macro, p, 6 * N * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));

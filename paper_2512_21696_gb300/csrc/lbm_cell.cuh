@@ -15,6 +15,9 @@
 // its post-collision populations into the slots of its neighbours.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "lbm_common.cuh"
 
 namespace lbm {
@@ -202,19 +205,182 @@ __device__ __forceinline__ float normal_divergence(const float g[3], const HessS
     return is * ((Hxx + Hyy + Hzz) - gHg * is * is);
 }
 
+// ---- shifted 16-bit storage (FP16 / BF16) -----------------------------------
+// Slot i of cell x holds f_i - w_i rho0 (i = 0..18, push form as in F32); all
+// arithmetic is FP32.
+struct H16 {
+    using T = __half;
+    static __device__ __forceinline__ float ld(T v) { return __half2float(v); }
+    static __device__ __forceinline__ T st(float x) { return __float2half_rn(x); }
+};
+struct B16 {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float ld(T v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ T st(float x) { return __float2bfloat16_rn(x); }
+};
+
+// Moments of one component from its 19 shifted 16-bit slots h_i = f_i - w_i rho0,
+// relative to the reference rest population f_r = rho/3 (so dr = 0 and
+// S = sum c c h + (rho0 - rho)/3 I).  rho = rho0 + sum_i h_i.
+template <class H>
+__device__ __forceinline__ CompMom moments_lp(const typename H::T *__restrict__ fa, size_t n, float rho0)
+{
+    float s = H::ld(fa[0]);
+    float j0 = 0.f, j1 = 0.f, j2 = 0.f, sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const float h = H::ld(fa[(size_t)i * n]);
+        s += h;
+        if (cx(i)) { j0 += cx(i) * h; sxx += h; }
+        if (cy(i)) { j1 += cy(i) * h; syy += h; }
+        if (cz(i)) { j2 += cz(i) * h; szz += h; }
+        if (cx(i) && cy(i)) sxy += cx(i) * cy(i) * h;
+        if (cx(i) && cz(i)) sxz += cx(i) * cz(i) * h;
+        if (cy(i) && cz(i)) syz += cy(i) * cz(i) * h;
+    }
+    CompMom m;
+    const float rho = rho0 + s;
+    const float dd = (rho0 - rho) * (1.0f / 3.0f);
+    m.dr = 0.f;
+    m.rho = {rho, 0.f};
+    m.j[0] = {j0, 0.f};
+    m.j[1] = {j1, 0.f};
+    m.j[2] = {j2, 0.f};
+    m.S[0] = sxx + dd;
+    m.S[1] = syy + dd;
+    m.S[2] = szz + dd;
+    m.S[3] = sxy;
+    m.S[4] = sxz;
+    m.S[5] = syz;
+    m.Ij[0] = m.Ij[1] = m.Ij[2] = 0;
+    return m;
+}
+// rho of one component from its 19 slots (same summation order as moments_lp).
+template <class H>
+__device__ __forceinline__ float density_lp(const typename H::T *__restrict__ fa, size_t n, float rho0)
+{
+    float s = H::ld(fa[0]);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) s += H::ld(fa[(size_t)i * n]);
+    return rho0 + s;
+}
+__device__ __forceinline__ float atwood_rho(int w, float rA, float rB)
+{
+    const float nw = w == 0 ? rA : rB, nn = w == 0 ? rB : rA;
+    const float den = nw + nn;
+    return den > 0.f ? __fdividef(nw - nn, den) : 0.f;
+}
+// Store of the post-collision state in a shifted 16-bit layout.
+template <class H>
+struct StoreLP {
+    typename H::T *fout;
+    int n, c;
+    float f0r[2];   // reference rest populations rho/3
+    float rho0[2];
+    float fnew[2];  // new rest populations
+    __device__ __forceinline__ float rest(int a, float d0)
+    {
+        fnew[a] = f0r[a] + d0;
+        fout[(size_t)a * Q * n + c] = H::st(fnew[a] - rho0[a] * (1.0f / 3.0f));
+        return 0.f;
+    }
+    __device__ __forceinline__ void pair(int a, int i, size_t ti, size_t tj, float E, float O)
+    {
+        const float b = w3(i) * fnew[a] - wgt(i) * rho0[a];
+        typename H::T *fo = fout + (size_t)a * Q * n;
+        fo[ti] = H::st(b + E + O);
+        fo[tj] = H::st(b + E - O);
+    }
+};
+
+// ---- rest-referenced layouts ----------------------------------------------
+// The state of a cell is its rest population f_0 (int32, 2^-30 fixed point)
+// and the 18 arrived populations relative to their sources' rest populations,
+// g_i = f_i - 3 w_i f_0(s).  LayF32 keeps g in FP32 in slots 1..18 of
+// [a][19][n] (slot 0 holds the int32 f_0); LayR16 keeps f_0 in an int32 array
+// [2][n] followed by g * 2^GS in 16 bits, [2][18][n].  g is small (the
+// velocity and non-equilibrium parts only), which is what makes 16 bits
+// usable; the power-of-two scale keeps FP16 values out of its subnormal range.
+struct LayF32 {
+    const float *in;
+    float *out;
+    int n;
+    __device__ __forceinline__ int rest_in(int a, int g) const
+    {
+        return reinterpret_cast<const int *>(in)[(size_t)a * Q * n + g];
+    }
+    __device__ __forceinline__ float mov_in(int a, int i, int g) const
+    {
+        return in[(size_t)a * Q * n + (size_t)i * n + g];
+    }
+    __device__ __forceinline__ void rest_out(int a, int c, int v) const
+    {
+        reinterpret_cast<int *>(out)[(size_t)a * Q * n + c] = v;
+    }
+    // slot = i n + cell, i >= 1
+    __device__ __forceinline__ void mov_out(int a, size_t slot, float v) const { out[(size_t)a * Q * n + slot] = v; }
+};
+template <class H, int GS>
+struct LayR16 {
+    const int *rin;
+    const typename H::T *min;
+    int *rout;
+    typename H::T *mout;
+    int n;
+    static constexpr float SC = (float)(1 << GS), ISC = 1.0f / (float)(1 << GS);
+    __device__ __forceinline__ int rest_in(int a, int g) const { return rin[(size_t)a * n + g]; }
+    __device__ __forceinline__ float mov_in(int a, int i, int g) const
+    {
+        return H::ld(min[((size_t)a * (Q - 1) + (i - 1)) * n + g]) * ISC;
+    }
+    __device__ __forceinline__ void rest_out(int a, int c, int v) const { rout[(size_t)a * n + c] = v; }
+    __device__ __forceinline__ void mov_out(int a, size_t slot, float v) const
+    {
+        mout[(size_t)a * (Q - 1) * n + slot - n] = H::st(v * SC);
+    }
+};
+using LayF16R = LayR16<H16, 12>;
+using LayB16R = LayR16<B16, 0>;
+
+// Store of the post-collision state of one cell in a rest-referenced layout:
+// the new rest population f_0 + d0 is added in fixed point, its sub-grid
+// residual goes into the moving populations (returned to the caller, which
+// adds 3 w_i res to each); direction i stores E + O, its opposite E - O.
+template <class LY>
+struct StoreRest {
+    LY ly;
+    int c;
+    int f0i[2];
+    __device__ __forceinline__ float rest(int a, float d0)
+    {
+        const float xq = d0 * FIX_ONE;
+        const float qf = rintf(xq);
+        ly.rest_out(a, c, f0i[a] + (int)qf);
+        return (xq - qf) * FIX_INV;
+    }
+    __device__ __forceinline__ void pair(int a, int i, size_t ti, size_t tj, float E, float O)
+    {
+        ly.mov_out(a, ti, E + O);
+        ly.mov_out(a, tj, E - O);
+    }
+};
+
 // Forces, residual update, velocity and the regularised collision of one
-// fluid cell, then the store of the new state (and of the fields if MACRO).
-//   f0i  rest populations (fixed point) of the cell; M its moments;
+// fluid cell, then the store of the new state through st (and of the fields
+// if MACRO).  The moments are relative to a reference rest population f_r:
+// M.dr = rho - 3 f_r and M.S = sum_i c_i c_i (f_i - 3 w_i f_r); the stored
+// post-collision populations are f*_0 = f_r + d0 and
+// f*_i = 3 w_i f*_0 + E_i +- O_i.
+//   M    the cell's moments;
 //   gf   FP32 parts of grad(rho^A), grad(rho^B); gAt grad(At) (gray cells);
 //   csf  whether Eq. 4 applies here; hA, hB the Hessian sums of rho^A, rho^B.
 //   tgt  tgt(i): offset within a component's array where direction i goes,
 //        i n + (index of x + c_i), or opp(i) n + c when x + c_i is solid.
-template <bool MACRO, class Target>
-__device__ __forceinline__ void collide_store(const DevParams &P, uint8_t t, int c, int n, const int f0i[2],
+template <bool MACRO, class Store, class Target>
+__device__ __forceinline__ void collide_store(const DevParams &P, uint8_t t, int c, int n, Store &st,
                                               const CompMom M[2], const float gf[2][3], const float gAt[3],
                                               bool csf, const HessSum &hA, const HessSum &hB,
-                                              GrayRec *__restrict__ gray,
-                                              float *__restrict__ fout, float *__restrict__ macro,
+                                              GrayRec *__restrict__ gray, float *__restrict__ macro,
                                               const Target &tgt)
 {
     const float r[2] = {M[0].rho.hi, M[1].rho.hi};
@@ -367,14 +533,9 @@ __device__ __forceinline__ void collide_store(const DevParams &P, uint8_t t, int
         const float Pxz = S[4] - ra * u[0] * u[2] + 0.5f * (u[0] * Fa[2] + Fa[0] * u[2]);
         const float Pyz = S[5] - ra * u[1] * u[2] + 0.5f * (u[1] * Fa[2] + Fa[1] * u[2]);
         const float trP = Pxx + Pyy + Pzz;
-        // f*_0 - f_0 = drho/3 - rho u^2/2 - om tr(Pi1)/2 - u.F/2, added exactly in
-        // fixed point; the sub-grid residual goes into the moving populations.
+        // f*_0 - f_r = drho/3 - rho u^2/2 - om tr(Pi1)/2 - u.F/2
         const float d0 = d3 - 0.5f * ra * uu - 0.5f * om * trP - 0.5f * uF;
-        const float xq = d0 * FIX_ONE;
-        const float qf = rintf(xq);
-        const float res = (xq - qf) * FIX_INV;
-        float *fo = fout + (size_t)a * Q * n;
-        reinterpret_cast<int *>(fo)[c] = f0i[a] + (int)qf;
+        const float res = st.rest(a, d0);
         // opposite pairs (i, i+1): cu, cF change sign, cPc does not, so
         // g_i = E + O and g_{i+1} = E - O
 #pragma unroll
@@ -390,8 +551,7 @@ __device__ __forceinline__ void collide_store(const DevParams &P, uint8_t t, int
             if (cy(i) && cz(i)) cPc += 2.0f * cy(i) * cz(i) * Pyz;
             const float E = wgt(i) * (4.5f * ra * cu * cu + 4.5f * om * cPc + 4.5f * cu * cF + 3.0f * res);
             const float O = wgt(i) * (3.0f * ra * cu + 1.5f * cF);
-            fo[tgt(i)] = E + O;
-            fo[tgt(i + 1)] = E - O;
+            st.pair(a, i, tgt(i), tgt(i + 1), E, O);
         }
     }
     if (MACRO) {

@@ -65,6 +65,8 @@ struct DevParams {
     float r_lo, inv_r_span;
     float s_lo, s_hi, at_cut, eps_n, kr_min;
     float at_wall;         // Atwood number of the wall densities
+    float rho0[2];         // shift of the 16-bit storages: f_i - w_i rho0
+    int storage;           // enum lbm_storage
     Curve curve[MAX_TYPES];
 };
 

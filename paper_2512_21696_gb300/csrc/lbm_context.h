@@ -7,7 +7,9 @@
 #include <string>
 #include <vector>
 
-#include "lbm_common.cuh"
+#include <type_traits>
+
+#include "lbm_cell.cuh"
 
 struct lbm_ctx {
     lbm_params p;
@@ -18,7 +20,7 @@ struct lbm_ctx {
     lbm_constitutive curves[LBM_MAX_PORE_TYPES];
 
     // device buffers (owned)
-    float *f[2] = {nullptr, nullptr};  // populations [2][19][n], ping-pong
+    float *f[2] = {nullptr, nullptr};  // populations [2][19][n] (F32 or 16-bit slots), ping-pong
     int cur = 0;                       // buffer holding the latest state
     uint8_t *type = nullptr;           // [n]
     float *phi = nullptr;              // [n] porosity (1 pore, 0 solid)
@@ -51,9 +53,23 @@ cudaError_t launch_init(lbm_ctx *ctx, const float *rhoA, const float *rhoB, cons
 cudaError_t launch_density(lbm_ctx *ctx);
 cudaError_t launch_collide(lbm_ctx *ctx, bool write_macro);
 cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro);
+cudaError_t launch_fused_lp(lbm_ctx *ctx, bool write_macro);
 cudaError_t launch_geometry(lbm_ctx *ctx, const uint8_t *ptype);
 cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16);
 cudaError_t launch_static_out(lbm_ctx *ctx, float *kinv6, float *pcs, float *swirr, float *sores);
+
+// Rest-referenced 16-bit layout views of population buffers bi (in) and bo
+// (out): int32 rest populations [2][n] first, then the 16-bit slots.
+template <class LY>
+inline LY lay_r16(lbm_ctx *ctx, int bi, int bo)
+{
+    using E = typename std::remove_pointer<decltype(LY::mout)>::type;
+    const size_t n = (size_t)ctx->n;
+    const char *pi = reinterpret_cast<const char *>(ctx->f[bi]);
+    char *po = reinterpret_cast<char *>(ctx->f[bo]);
+    return LY{reinterpret_cast<const int *>(pi), reinterpret_cast<const E *>(pi + 2 * n * sizeof(int)),
+              reinterpret_cast<int *>(po), reinterpret_cast<E *>(po + 2 * n * sizeof(int)), ctx->n};
+}
 
 // Profiling helpers used around launches.
 void prof_begin(lbm_ctx *ctx, const char *name, cudaEvent_t *ev_out);

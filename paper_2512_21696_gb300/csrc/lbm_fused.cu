@@ -57,10 +57,10 @@ __device__ __forceinline__ int wrap_coord(int v, int n, int per)
 }
 __device__ __forceinline__ int ring3(int p) { return ((p % 3) + 3) % 3; }
 
-template <int TX, int TY, int MINB, bool MACRO>
+template <int TX, int TY, int MINB, bool MACRO, class LY>
 __global__ void __launch_bounds__(TX *TY, MINB)
-    k_fused(DevParams P, int zchunks, const float *__restrict__ fin, float *__restrict__ fout,
-            const uint8_t *__restrict__ type, GrayRec *__restrict__ gray, float *__restrict__ macro)
+    k_fused(DevParams P, int zchunks, LY ly, const uint8_t *__restrict__ type, GrayRec *__restrict__ gray,
+            float *__restrict__ macro)
 {
     using T = Tiles<TX, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -71,8 +71,6 @@ __global__ void __launch_bounds__(TX *TY, MINB)
 
     const int n = P.n;
     const int tid = threadIdx.x;
-    const int *fiA = reinterpret_cast<const int *>(fin);
-    const int *fiB = reinterpret_cast<const int *>(fin + (size_t)Q * n);
     const int tiles_x = (P.nx + TX - 1) / TX, tiles_y = (P.ny + TY - 1) / TY;
     const int ncol = tiles_x * tiles_y;
 
@@ -96,8 +94,8 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                     const int g = gx + P.nx * (gy + P.ny * gz);
                     rc.type = type[g];
                     if (rc.type != CELL_SOLID) {
-                        rc.f0A = fiA[g];
-                        rc.f0B = fiB[g];
+                        rc.f0A = ly.rest_in(0, g);
+                        rc.f0B = ly.rest_in(1, g);
                     }
                 }
                 dst[e] = rc;
@@ -123,7 +121,6 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                         P.nx * (wrap_coord(y0 - 1 + dy, P.ny, P.per[1]) + P.ny * gz);
 #pragma unroll
                     for (int a = 0; a < 2; ++a) {
-                        const float *fa = fin + (size_t)a * Q * n + g;
                         const int f0 = a ? me.f0B : me.f0A;
                         float acc = 0.f;
                         long long id = 0;
@@ -132,7 +129,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                             const int o = opp(i);  // the source x - c_i is x + c_o
                             const RawCell *rp = cz(o) < 0 ? r0 : (cz(o) > 0 ? r2 : r1);
                             const RawCell &src = rp[(dx + 1 + cx(o)) + T::RX * (dy + 1 + cy(o))];
-                            acc += fa[(size_t)i * n];
+                            acc += ly.mov_in(a, i, g);
                             if (src.type != CELL_SOLID) id += (long long)((a ? src.f0B : src.f0A) - f0) * w12(i);
                         }
                         const float v = ff_add_f(ff_twelfth(id), acc).hi;
@@ -179,7 +176,6 @@ __global__ void __launch_bounds__(TX *TY, MINB)
             CompMom M[2];
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
-                const float *fa = fin + (size_t)a * Q * n + c;
                 PullSums p;
                 pull_zero(p);
 #pragma unroll
@@ -190,7 +186,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                         const DenCell &sd = (cz(o) < 0 ? d0p : (cz(o) > 0 ? d2 : d1))[dk + cx(o) + T::DX * cy(o)];
                         dfi = (a ? sd.f0B : sd.f0A) - f0i[a];
                     }
-                    pull_add(p, i, fa[(size_t)i * n], dfi);
+                    pull_add(p, i, ly.mov_in(a, i, c), dfi);
                 }
                 M[a] = finish_moments(p, f0i[a]);
             }
@@ -222,7 +218,8 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                 const DenMeta &tm = (cz(i) < 0 ? m0 : (cz(i) > 0 ? m2 : m1))[dk + cx(i) + T::DX * cy(i)];
                 return (size_t)i * n + tm.gidx;
             };
-            collide_store<MACRO>(P, t, c, n, f0i, M, gf, gAt, csf, hA, hB, gray, fout, macro, tgt);
+            StoreRest<LY> st{ly, c, {f0i[0], f0i[1]}};
+            collide_store<MACRO>(P, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
         };
 
         load_raw(za - 2);
@@ -239,10 +236,10 @@ __global__ void __launch_bounds__(TX *TY, MINB)
 }
 
 // ---------------------------------------------------------------------------
-template <int TX, int TY, int MINB, bool MACRO>
-static cudaError_t launch_fused_t(lbm_ctx *ctx)
+template <int TX, int TY, int MINB, bool MACRO, class LY>
+static cudaError_t launch_fused_t(lbm_ctx *ctx, LY ly)
 {
-    auto kern = k_fused<TX, TY, MINB, MACRO>;
+    auto kern = k_fused<TX, TY, MINB, MACRO, LY>;
     const size_t smem = Tiles<TX, TY>::smem();
     // launch configuration, resolved once per device
     static int cached_slots[64] = {};  // resident CTAs per device
@@ -262,35 +259,38 @@ static cudaError_t launch_fused_t(lbm_ctx *ctx)
     const int slots = cached_slots[dev];
     const int zchunks = (int)std::max<long long>(1, std::min<long long>(slots / ncol, ctx->p.nz));
     const long long grid = std::min<long long>(ncol * zchunks, slots);
-    const float *fin = ctx->f[ctx->cur];
-    float *fout = ctx->f[1 - ctx->cur];
     cudaEvent_t e0;
     prof_begin(ctx, "k_fused", &e0);
-    kern<<<(unsigned)grid, TX * TY, smem, ctx->stream>>>(ctx->dp, zchunks, fin, fout, ctx->type, ctx->gray,
-                                                         ctx->macro);
+    kern<<<(unsigned)grid, TX * TY, smem, ctx->stream>>>(ctx->dp, zchunks, ly, ctx->type, ctx->gray, ctx->macro);
     prof_end(ctx, "k_fused", e0);
     ctx->launches += 1;
     ctx->cur = 1 - ctx->cur;
     return cudaGetLastError();
 }
 
-template <int TX, int TY, int MINB>
-static cudaError_t launch_fused_tile(lbm_ctx *ctx, bool write_macro)
+template <int TX, int TY, int MINB, class LY>
+static cudaError_t launch_fused_tile(lbm_ctx *ctx, bool write_macro, LY ly)
 {
-    return write_macro ? launch_fused_t<TX, TY, MINB, true>(ctx) : launch_fused_t<TX, TY, MINB, false>(ctx);
+    return write_macro ? launch_fused_t<TX, TY, MINB, true>(ctx, ly) : launch_fused_t<TX, TY, MINB, false>(ctx, ly);
 }
 
 // Tile variants: 0 = 32x8 (one CTA per SM, no register cap), 1 = 32x16
 // (128 registers), 2 = 32x8 with two CTAs per SM (128 registers), 3 = 32x12
 // (168 registers), 4 = 64x8 (128 registers).
+// The rest-referenced 16-bit layouts run the default tile.
 cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro)
 {
+    if (ctx->p.storage == LBM_STORAGE_F16R)
+        return launch_fused_tile<32, 8, 2>(ctx, write_macro, lay_r16<LayF16R>(ctx, ctx->cur, 1 - ctx->cur));
+    if (ctx->p.storage == LBM_STORAGE_BF16R)
+        return launch_fused_tile<32, 8, 2>(ctx, write_macro, lay_r16<LayB16R>(ctx, ctx->cur, 1 - ctx->cur));
+    const LayF32 ly{ctx->f[ctx->cur], ctx->f[1 - ctx->cur], ctx->n};
     switch (ctx->tile) {
-    case 1: return launch_fused_tile<32, 16, 1>(ctx, write_macro);
-    case 2: return launch_fused_tile<32, 8, 2>(ctx, write_macro);
-    case 3: return launch_fused_tile<32, 12, 1>(ctx, write_macro);
-    case 4: return launch_fused_tile<64, 8, 1>(ctx, write_macro);
-    default: return launch_fused_tile<32, 8, 1>(ctx, write_macro);
+    case 1: return launch_fused_tile<32, 16, 1>(ctx, write_macro, ly);
+    case 2: return launch_fused_tile<32, 8, 2>(ctx, write_macro, ly);
+    case 3: return launch_fused_tile<32, 12, 1>(ctx, write_macro, ly);
+    case 4: return launch_fused_tile<64, 8, 1>(ctx, write_macro, ly);
+    default: return launch_fused_tile<32, 8, 1>(ctx, write_macro, ly);
     }
 }
 

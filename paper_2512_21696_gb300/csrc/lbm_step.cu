@@ -54,20 +54,46 @@ __device__ __forceinline__ int nb_index(const DevParams &P, const Axes &A, int i
     return (X < 0 || Y < 0 || Z < 0) ? -1 : X + P.nx * (Y + P.ny * Z);
 }
 
+// Fields of the initial state and the residual flag of gray cells (wet where
+// s >= 1/2).
+__device__ __forceinline__ void init_fields_out(const DevParams &P, int c, uint8_t t, const double r[2],
+                                                const double uv[3], float *__restrict__ macro,
+                                                GrayRec *__restrict__ gray)
+{
+    const int n = P.n;
+    const double rw = r[P.wet], rn = r[1 - P.wet];
+    double s = ((rw / (rw + rn)) - (double)P.r_lo) * (double)P.inv_r_span;
+    s = s < 0.0 ? 0.0 : (s > 1.0 ? 1.0 : s);
+    macro[c] = (float)r[0];
+    macro[(size_t)n + c] = (float)r[1];
+    macro[(size_t)2 * n + c] = (float)uv[0];
+    macro[(size_t)3 * n + c] = (float)uv[1];
+    macro[(size_t)4 * n + c] = (float)uv[2];
+    macro[(size_t)5 * n + c] = (float)s;
+    if (t == CELL_GRAY) {
+        unsigned meta = __float_as_uint(gray[c].b.w) & 0xffu;
+        if (s >= 0.5) meta |= META_WET;
+        gray[c].b.w = __uint_as_float(meta);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Initial state: equilibrium of (rhoA, rhoB, u), evaluated in FP64 once.
 // ---------------------------------------------------------------------------
+template <class LY>
 __global__ void k_init(DevParams P, const float *__restrict__ rhoA, const float *__restrict__ rhoB,
-                       const float *__restrict__ u, const uint8_t *__restrict__ type,
-                       float *__restrict__ f, float *__restrict__ drho, float *__restrict__ macro,
-                       GrayRec *__restrict__ gray)
+                       const float *__restrict__ u, const uint8_t *__restrict__ type, LY ly,
+                       float *__restrict__ drho, float *__restrict__ macro, GrayRec *__restrict__ gray)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = P.n;
     if (c >= n) return;
     const uint8_t t = type[c];
     if (t == CELL_SOLID) {
-        for (int k = 0; k < 2 * Q; ++k) f[(size_t)k * n + c] = 0.0f;
+        for (int a = 0; a < 2; ++a) {
+            ly.rest_out(a, c, 0);
+            for (int i = 1; i < Q; ++i) ly.mov_out(a, (size_t)i * n + c, 0.0f);
+        }
         drho[c] = 0.0f;
         drho[n + c] = 0.0f;
         drho[(size_t)2 * n + c] = P.at_wall;
@@ -86,11 +112,10 @@ __global__ void k_init(DevParams P, const float *__restrict__ rhoA, const float 
     const double uu = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
     const double r[2] = {(double)rhoA[c], (double)rhoB[c]};
     for (int a = 0; a < 2; ++a) {
-        float *fa = f + (size_t)a * Q * n;
         const double f0 = r[a] / 3.0 - 0.5 * r[a] * uu;  // feq_0 = w_0 rho (1 - 3u^2/2)
         const long long q = llrint(f0 * FIX_ONE_D);
         const double r0 = f0 - (double)q / FIX_ONE_D;
-        reinterpret_cast<int *>(fa)[c] = (int)q;
+        ly.rest_out(a, c, (int)q);
         // the equilibrium populations, streamed: direction i goes to x + c_i,
         // or back into the cell's own opposite slot when x + c_i is solid
 #pragma unroll
@@ -99,24 +124,54 @@ __global__ void k_init(DevParams P, const float *__restrict__ rhoA, const float 
             const double g = wgt_d(i) * (r[a] * (3.0 * cu + 4.5 * cu * cu) + 3.0 * r0);
             const int m = nb_index(P, A, i);
             const bool wl = m < 0 || type[m] == CELL_SOLID;
-            fa[wl ? (size_t)opp(i) * n + c : (size_t)i * n + m] = (float)g;
+            ly.mov_out(a, wl ? (size_t)opp(i) * n + c : (size_t)i * n + m, (float)g);
         }
         drho[(size_t)a * n + c] = 0.0f;
     }
-    const double rw = r[P.wet], rn = r[1 - P.wet];
-    double s = ((rw / (rw + rn)) - (double)P.r_lo) * (double)P.inv_r_span;
-    s = s < 0.0 ? 0.0 : (s > 1.0 ? 1.0 : s);
-    macro[c] = (float)r[0];
-    macro[(size_t)n + c] = (float)r[1];
-    macro[(size_t)2 * n + c] = (float)uv[0];
-    macro[(size_t)3 * n + c] = (float)uv[1];
-    macro[(size_t)4 * n + c] = (float)uv[2];
-    macro[(size_t)5 * n + c] = (float)s;
-    if (t == CELL_GRAY) {
-        unsigned meta = __float_as_uint(gray[c].b.w) & 0xffu;
-        if (s >= 0.5) meta |= META_WET;
-        gray[c].b.w = __uint_as_float(meta);
+    init_fields_out(P, c, t, r, uv, macro, gray);
+}
+
+// Initial state in a shifted 16-bit storage: h_i = f^eq_i - w_i rho0, pushed
+// like the F32 state.
+template <class H>
+__global__ void k_init_lp(DevParams P, const float *__restrict__ rhoA, const float *__restrict__ rhoB,
+                          const float *__restrict__ u, const uint8_t *__restrict__ type,
+                          typename H::T *__restrict__ f, float *__restrict__ macro, GrayRec *__restrict__ gray)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = P.n;
+    if (c >= n) return;
+    const uint8_t t = type[c];
+    if (t == CELL_SOLID) {
+        for (int k = 0; k < 2 * Q; ++k) f[(size_t)k * n + c] = H::st(0.0f);
+        for (int k = 0; k < 6; ++k) macro[(size_t)k * n + c] = 0.0f;
+        return;
     }
+    int x, y, z;
+    cell_xyz(c, P, x, y, z);
+    const Axes A = axes_of(P, x, y, z);
+    double uv[3] = {0.0, 0.0, 0.0};
+    if (u) {
+        uv[0] = u[c];
+        uv[1] = u[(size_t)n + c];
+        uv[2] = u[(size_t)2 * n + c];
+    }
+    const double uu = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
+    const double r[2] = {(double)rhoA[c], (double)rhoB[c]};
+    for (int a = 0; a < 2; ++a) {
+        typename H::T *fa = f + (size_t)a * Q * n;
+        const double r0 = (double)P.rho0[a];
+        fa[c] = H::st((float)(wgt_d(0) * (r[a] * (1.0 - 1.5 * uu) - r0)));
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const double cu = cx(i) * uv[0] + cy(i) * uv[1] + cz(i) * uv[2];
+            const double h = wgt_d(i) * (r[a] * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu) - r0);
+            const int m = nb_index(P, A, i);
+            const bool wl = m < 0 || type[m] == CELL_SOLID;
+            fa[wl ? (size_t)opp(i) * n + c : (size_t)i * n + m] = H::st((float)h);
+        }
+    }
+    init_fields_out(P, c, t, r, uv, macro, gray);
 }
 
 // ---------------------------------------------------------------------------
@@ -241,7 +296,8 @@ __global__ void __launch_bounds__(256) k_collide(DevParams P, const float *__res
     auto tgt = [&](int i) -> size_t {
         return (wall & (1u << i)) ? (size_t)opp(i) * n + c : (size_t)i * n + nb[i];
     };
-    collide_store<MACRO>(P, t, c, n, f0i, M, gf, gAt, csf, hA, hB, gray, fout, macro, tgt);
+    StoreRest<LayF32> st{LayF32{fin, fout, n}, c, {f0i[0], f0i[1]}};
+    collide_store<MACRO>(P, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
 }
 
 // ---------------------------------------------------------------------------
@@ -253,9 +309,25 @@ cudaError_t launch_init(lbm_ctx *ctx, const float *rhoA, const float *rhoB, cons
 {
     cudaEvent_t e0;
     prof_begin(ctx, "k_init", &e0);
-    k_init<<<grid_for(ctx->n, 256), 256, 0, ctx->stream>>>(ctx->dp, rhoA, rhoB, u, ctx->type,
-                                                          ctx->f[ctx->cur], ctx->rho, ctx->macro,
-                                                          ctx->gray);
+    if (ctx->p.storage == LBM_STORAGE_F16S)
+        k_init_lp<H16><<<grid_for(ctx->n, 256), 256, 0, ctx->stream>>>(
+            ctx->dp, rhoA, rhoB, u, ctx->type, reinterpret_cast<__half *>(ctx->f[ctx->cur]), ctx->macro, ctx->gray);
+    else if (ctx->p.storage == LBM_STORAGE_BF16S)
+        k_init_lp<B16><<<grid_for(ctx->n, 256), 256, 0, ctx->stream>>>(
+            ctx->dp, rhoA, rhoB, u, ctx->type, reinterpret_cast<__nv_bfloat16 *>(ctx->f[ctx->cur]), ctx->macro,
+            ctx->gray);
+    else if (ctx->p.storage == LBM_STORAGE_F16R)
+        k_init<<<grid_for(ctx->n, 256), 256, 0, ctx->stream>>>(ctx->dp, rhoA, rhoB, u, ctx->type,
+                                                              lay_r16<LayF16R>(ctx, ctx->cur, ctx->cur), ctx->rho,
+                                                              ctx->macro, ctx->gray);
+    else if (ctx->p.storage == LBM_STORAGE_BF16R)
+        k_init<<<grid_for(ctx->n, 256), 256, 0, ctx->stream>>>(ctx->dp, rhoA, rhoB, u, ctx->type,
+                                                              lay_r16<LayB16R>(ctx, ctx->cur, ctx->cur), ctx->rho,
+                                                              ctx->macro, ctx->gray);
+    else
+        k_init<<<grid_for(ctx->n, 256), 256, 0, ctx->stream>>>(
+            ctx->dp, rhoA, rhoB, u, ctx->type, LayF32{ctx->f[ctx->cur], ctx->f[ctx->cur], ctx->n}, ctx->rho,
+            ctx->macro, ctx->gray);
     prof_end(ctx, "k_init", e0);
     ctx->launches += 1;
     return cudaGetLastError();

@@ -160,3 +160,16 @@ def drainage(n=128, seed=synth.SEED_BASE + 1):
     rA, rB = synth.drainage_fields(cell, 1.0, 0.03)
     return Case(f"drainage{n}", (n, n, n), cell, phi, rA, rB, ptype=ptype, G=1.1, kappa=-0.045,
                 accel=((1e-5, 0, 0), (0, 0, 0)), rho_wall=(0.03, 1.0), wet=1)
+
+
+def fiber_flow(n=24, axis=0, seed=synth.SEED_BASE + 2, ncyl=12, aniso=10.0, g=1e-5):
+    """Fibre-bundle permeability (tensorial resistivity, anisotropy 10): wetting
+    B at rho_hi everywhere with A dissolved at rho_lo, body acceleration g on
+    B along `axis`.  Darcy: K_axis = <u_axis> nu / g with <u> over all cells."""
+    cell, phi, ptype, _ = synth.fiber_bundle_geometry(n, seed, ncyl=ncyl)
+    shape = cell.shape
+    acc = [0.0, 0.0, 0.0]
+    acc[axis] = g
+    return Case(f"fiber{n}_{'xyz'[axis]}", shape, cell, phi, np.full(shape, 0.03), np.full(shape, 1.0),
+                ptype=ptype, curves=[dict(CURVE, aniso=aniso)], G=1.1, accel=((0, 0, 0), tuple(acc)),
+                rho_wall=(0.03, 1.0), wet=1)
