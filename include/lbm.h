@@ -249,6 +249,41 @@ LBM_API int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *c
  * LBM_ERR_ARG on unknown values. */
 LBM_API int lbm_set_kernel(lbm_ctx *ctx, int path, int tile);
 
+/* ---- Batches of lattices (REV library runs, workflow step ii) -----------
+ * A batch advances many independent lattices of uneven size together: one
+ * persistent launch per step (and tile shape in use) takes (run, column,
+ * z-chunk) items from a device work counter, k steps are captured once into
+ * a CUDA graph and replayed.  The paper runs its REV library one simulation
+ * at a time; batching is this library's own scheduling and changes no
+ * arithmetic (a run advanced in a batch equals the run advanced alone).
+ *
+ * lbm_batch_create: runs[nruns] give each lattice's shape, body acceleration
+ *   and probe; all other fields must be equal (LBM_ERR_ARG otherwise), and
+ *   storage must be F32, F16R or BF16R.  Device buffers are owned by the
+ *   batch.
+ * lbm_batch_run: the context of one run, a view of the batch's buffers: use
+ *   it with lbm_set_constitutive, lbm_set_geometry, lbm_init_fields,
+ *   lbm_observables, lbm_get_fields, lbm_get_static and checkpoints (and
+ *   lbm_step to advance that run alone).  lbm_destroy refuses it; it lives
+ *   until lbm_batch_destroy.
+ * lbm_batch_step: nsteps steps of every run (LBM_ERR_STATE unless every run
+ *   has fields at the same step parity).  Asynchronous; the first call with a
+ *   given nsteps and parity captures the graph.
+ * lbm_batch_tune: for the runs of each x extent, times trial_steps steps
+ *   (rounded up to even) of every tile shape (0 = 32x8, 1 = 16x16,
+ *   2 = 32x16) and keeps the fastest; the state is restored afterwards.
+ *   tiles_out (nruns entries, may be NULL) receives the choice per run.
+ *   Synchronous.
+ * lbm_batch_info: total cells, steps taken, kernels launched by
+ *   lbm_batch_step, and the number of launches per step. */
+typedef struct lbm_batch lbm_batch;
+LBM_API int lbm_batch_create(lbm_batch **out, int nruns, const lbm_params *runs);
+LBM_API int lbm_batch_destroy(lbm_batch *b);
+LBM_API int lbm_batch_run(lbm_batch *b, int run, lbm_ctx **view);
+LBM_API int lbm_batch_step(lbm_batch *b, int nsteps);
+LBM_API int lbm_batch_tune(lbm_batch *b, int trial_steps, int *tiles_out);
+LBM_API int lbm_batch_info(lbm_batch *b, long long *cells, long long *steps, long long *launches, int *ngroups);
+
 /* Number of kernels the context has launched since creation. */
 LBM_API int lbm_launch_count(lbm_ctx *ctx, long long *count);
 

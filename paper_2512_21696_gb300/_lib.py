@@ -83,6 +83,7 @@ EXPORTS = [
     "lbm_set_geometry", "lbm_init_fields", "lbm_step", "lbm_observables", "lbm_get_fields",
     "lbm_get_static", "lbm_state_size", "lbm_save_state", "lbm_load_state", "lbm_profile",
     "lbm_profile_read", "lbm_launch_count", "lbm_struct_size", "lbm_observables_noalloc", "lbm_set_kernel",
+    "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_run", "lbm_batch_step", "lbm_batch_tune", "lbm_batch_info",
 ]
 
 _lock = threading.Lock()
@@ -130,6 +131,13 @@ def load(build_if_needed: bool = True):
         lib.lbm_observables_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_double,
                                                 C.POINTER(C.c_double), vp, C.POINTER(lbm_obs)]
         lib.lbm_set_kernel.argtypes = [P, C.c_int, C.c_int]
+        lib.lbm_batch_create.argtypes = [C.POINTER(P), C.c_int, C.POINTER(lbm_params)]
+        lib.lbm_batch_destroy.argtypes = [P]
+        lib.lbm_batch_run.argtypes = [P, C.c_int, C.POINTER(P)]
+        lib.lbm_batch_step.argtypes = [P, C.c_int]
+        lib.lbm_batch_tune.argtypes = [P, C.c_int, C.POINTER(C.c_int)]
+        lib.lbm_batch_info.argtypes = [P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                       C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
         lib.lbm_struct_size.restype = C.c_size_t
         lib.lbm_struct_size.argtypes = [C.c_int]
         for name in EXPORTS:

@@ -7,43 +7,18 @@
 #include <vector>
 
 #include "lbm_context.h"
+#include "lbm_host.h"
 
-namespace lbm {
-int obs_blocks(int n);
-constexpr int NOBS_HOST = 16;
-}  // namespace lbm
-
-namespace {
+namespace lbm_host {
 
 thread_local char g_last_cuda_error[256] = "";
 
 int cuda_fail(cudaError_t e, const char *where)
 {
     std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", where, cudaGetErrorString(e));
+    (void)cudaGetLastError();  // a non-sticky error must not surface again at a later launch check
     return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
 }
-
-#define LBM_CUDA(call)                                   \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-    } while (0)
-
-// Makes the context's device current for the duration of a call.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 // Device buffer that is freed on scope exit (used for staging host inputs).
 struct Staging {
@@ -131,7 +106,26 @@ int stage_in(const void *src, size_t bytes, int mem, cudaStream_t s, Staging &st
     return LBM_OK;
 }
 
-}  // namespace
+int validate_params(const lbm_params *p)
+{
+    if (!p) return LBM_ERR_ARG;
+    const long long n = (long long)p->nx * p->ny * p->nz;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || n > (long long)INT32_MAX / 8) return LBM_ERR_ARG;
+    if (!(p->tau[0] > 0.5 && p->tau[1] > 0.5)) return LBM_ERR_ARG;
+    if (!(p->rho_hi > p->rho_lo && p->rho_lo > 0.0 && p->rho_hi <= 4.0)) return LBM_ERR_ARG;
+    if (!(p->phi_avg[0] > 0 && p->phi_avg[1] > 0 && p->phi_max[0] > 0 && p->phi_max[1] > 0)) return LBM_ERR_ARG;
+    if (p->wet_idx != 0 && p->wet_idx != 1) return LBM_ERR_ARG;
+    if (!(p->s_lo >= 0 && p->s_lo < p->s_hi && p->s_hi <= 1)) return LBM_ERR_ARG;
+    if (!(p->eps_n > 0 && p->kr_min > 0 && p->at_cut >= 0 && p->c_g >= 0)) return LBM_ERR_ARG;
+    if (p->storage < LBM_STORAGE_F32 || p->storage > LBM_STORAGE_BF16R) return LBM_ERR_ARG;
+    for (int a = 0; a < 2; ++a)
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(p->body_accel[a][k])) return LBM_ERR_ARG;
+    return LBM_OK;
+}
+
+}  // namespace lbm_host
+using namespace lbm_host;
 
 namespace lbm {
 
@@ -241,19 +235,9 @@ int lbm_create(lbm_ctx **out, const lbm_params *p)
 {
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
-    if (!p) return LBM_ERR_ARG;
+    const int vr = validate_params(p);
+    if (vr != LBM_OK) return vr;
     const long long n = (long long)p->nx * p->ny * p->nz;
-    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || n > (long long)INT32_MAX / 8) return LBM_ERR_ARG;
-    if (!(p->tau[0] > 0.5 && p->tau[1] > 0.5)) return LBM_ERR_ARG;
-    if (!(p->rho_hi > p->rho_lo && p->rho_lo > 0.0 && p->rho_hi <= 4.0)) return LBM_ERR_ARG;
-    if (!(p->phi_avg[0] > 0 && p->phi_avg[1] > 0 && p->phi_max[0] > 0 && p->phi_max[1] > 0)) return LBM_ERR_ARG;
-    if (p->wet_idx != 0 && p->wet_idx != 1) return LBM_ERR_ARG;
-    if (!(p->s_lo >= 0 && p->s_lo < p->s_hi && p->s_hi <= 1)) return LBM_ERR_ARG;
-    if (!(p->eps_n > 0 && p->kr_min > 0 && p->at_cut >= 0 && p->c_g >= 0)) return LBM_ERR_ARG;
-    if (p->storage < LBM_STORAGE_F32 || p->storage > LBM_STORAGE_BF16R) return LBM_ERR_ARG;
-    for (int a = 0; a < 2; ++a)
-        for (int k = 0; k < 3; ++k)
-            if (!std::isfinite(p->body_accel[a][k])) return LBM_ERR_ARG;
 
     lbm_ctx *ctx = new (std::nothrow) lbm_ctx();
     if (!ctx) return LBM_ERR_OOM;
@@ -288,6 +272,7 @@ int lbm_create(lbm_ctx **out, const lbm_params *p)
 int lbm_destroy(lbm_ctx *ctx)
 {
     if (!ctx) return LBM_OK;
+    if (ctx->view) return LBM_ERR_ARG;  // owned by its batch
     DeviceGuard g(ctx->dev);
     for (auto &r : ctx->prof) {
         cudaEventDestroy(r.a);

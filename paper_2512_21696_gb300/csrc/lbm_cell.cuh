@@ -293,6 +293,34 @@ struct StoreLP {
     }
 };
 
+// Shape of the lattice a march works on: sizes, cell count (the slot stride)
+// and body acceleration (per run in a batch, P's otherwise).
+struct Geo {
+    int nx, ny, nz, n;
+    float accel[2][3];
+};
+__device__ __forceinline__ Geo geo_of(const DevParams &P)
+{
+    Geo G;
+    G.nx = P.nx;
+    G.ny = P.ny;
+    G.nz = P.nz;
+    G.n = P.n;
+    for (int a = 0; a < 2; ++a)
+        for (int d = 0; d < 3; ++d) G.accel[a][d] = P.accel[a][d];
+    return G;
+}
+
+// One lattice of a batch (see k_fused_batch): its shape, the work items it
+// contributes, its offsets in the batch buffers and its body acceleration.
+struct BatchRun {
+    int nx, ny, nz, n;
+    int tiles_x, ncol, zchunks, item0;
+    long long cell_off;  // first cell of the run in the per-cell arrays
+    long long pop_off;   // byte offset of the run in each population buffer
+    float accel[2][3];
+};
+
 // ---- rest-referenced layouts ----------------------------------------------
 // The state of a cell is its rest population f_0 (int32, 2^-30 fixed point)
 // and the 18 arrived populations relative to their sources' rest populations,
@@ -319,6 +347,11 @@ struct LayF32 {
     }
     // slot = i n + cell, i >= 1
     __device__ __forceinline__ void mov_out(int a, size_t slot, float v) const { out[(size_t)a * Q * n + slot] = v; }
+    // view of the population buffers of an n-cell lattice starting at in / out
+    __host__ __device__ static LayF32 make(const void *in, void *out, int n)
+    {
+        return LayF32{reinterpret_cast<const float *>(in), reinterpret_cast<float *>(out), n};
+    }
 };
 template <class H, int GS>
 struct LayR16 {
@@ -337,6 +370,14 @@ struct LayR16 {
     __device__ __forceinline__ void mov_out(int a, size_t slot, float v) const
     {
         mout[(size_t)a * (Q - 1) * n + slot - n] = H::st(v * SC);
+    }
+    __host__ __device__ static LayR16 make(const void *in, void *out, int n)
+    {
+        using E = typename H::T;
+        const char *pi = reinterpret_cast<const char *>(in);
+        char *po = reinterpret_cast<char *>(out);
+        return LayR16{reinterpret_cast<const int *>(pi), reinterpret_cast<const E *>(pi + 2 * (size_t)n * sizeof(int)),
+                      reinterpret_cast<int *>(po), reinterpret_cast<E *>(po + 2 * (size_t)n * sizeof(int)), n};
     }
 };
 using LayF16R = LayR16<H16, 12>;
@@ -371,13 +412,15 @@ struct StoreRest {
 // M.dr = rho - 3 f_r and M.S = sum_i c_i c_i (f_i - 3 w_i f_r); the stored
 // post-collision populations are f*_0 = f_r + d0 and
 // f*_i = 3 w_i f*_0 + E_i +- O_i.
+//   acc  body acceleration per component (F = rho acc);
 //   M    the cell's moments;
 //   gf   FP32 parts of grad(rho^A), grad(rho^B); gAt grad(At) (gray cells);
 //   csf  whether Eq. 4 applies here; hA, hB the Hessian sums of rho^A, rho^B.
 //   tgt  tgt(i): offset within a component's array where direction i goes,
 //        i n + (index of x + c_i), or opp(i) n + c when x + c_i is solid.
 template <bool MACRO, class Store, class Target>
-__device__ __forceinline__ void collide_store(const DevParams &P, uint8_t t, int c, int n, Store &st,
+__device__ __forceinline__ void collide_store(const DevParams &P, const float (&acc)[2][3], uint8_t t, int c, int n,
+                                              Store &st,
                                               const CompMom M[2], const float gf[2][3], const float gAt[3],
                                               bool csf, const HessSum &hA, const HessSum &hB,
                                               GrayRec *__restrict__ gray, float *__restrict__ macro,
@@ -409,8 +452,8 @@ __device__ __forceinline__ void collide_store(const DevParams &P, uint8_t t, int
         Fsc[1][d] = ff_mul(Gff, ff_mul(M[1].rho, grA[d]));
         Fsc[0][d].hi = -Fsc[0][d].hi; Fsc[0][d].lo = -Fsc[0][d].lo;
         Fsc[1][d].hi = -Fsc[1][d].hi; Fsc[1][d].lo = -Fsc[1][d].lo;
-        F[0][d] = r[0] * P.accel[0][d];  // the remaining (small) force terms, FP32
-        F[1][d] = r[1] * P.accel[1][d];
+        F[0][d] = r[0] * acc[0][d];  // the remaining (small) force terms, FP32
+        F[1][d] = r[1] * acc[1][d];
     }
     // the cancelling part of the momentum balance, j + F_sc/2, in float-float;
     // the remaining forces are added to it in FP32 below

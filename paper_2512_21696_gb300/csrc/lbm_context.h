@@ -34,6 +34,7 @@ struct lbm_ctx {
     int tile = 2;   // fused tile variant (lbm_set_kernel); 2 = 32x8, two CTAs per SM
     bool has_geometry = false;
     bool has_fields = false;
+    bool view = false;  // a run of a batch: buffers owned by the batch
     long long steps = 0;
     long long launches = 0;
 
@@ -46,6 +47,11 @@ struct lbm_ctx {
 };
 
 namespace lbm {
+
+// Observables reduction: blocks of the partial sums for n cells, and the
+// number of FP64 values it returns.
+int obs_blocks(int n);
+constexpr int NOBS_HOST = 16;
 
 // Kernel launches (each records itself in ctx->launches and, while profiling,
 // brackets the launch with CUDA events).
@@ -63,12 +69,7 @@ cudaError_t launch_static_out(lbm_ctx *ctx, float *kinv6, float *pcs, float *swi
 template <class LY>
 inline LY lay_r16(lbm_ctx *ctx, int bi, int bo)
 {
-    using E = typename std::remove_pointer<decltype(LY::mout)>::type;
-    const size_t n = (size_t)ctx->n;
-    const char *pi = reinterpret_cast<const char *>(ctx->f[bi]);
-    char *po = reinterpret_cast<char *>(ctx->f[bo]);
-    return LY{reinterpret_cast<const int *>(pi), reinterpret_cast<const E *>(pi + 2 * n * sizeof(int)),
-              reinterpret_cast<int *>(po), reinterpret_cast<E *>(po + 2 * n * sizeof(int)), ctx->n};
+    return LY::make(ctx->f[bi], ctx->f[bo], ctx->n);
 }
 
 // Profiling helpers used around launches.

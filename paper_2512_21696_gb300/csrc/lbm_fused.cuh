@@ -1,0 +1,227 @@
+// Rolling-window march of the fused time step (shared by the one-lattice
+// kernel and the batched kernel): populations cross HBM once each way.
+//
+// Each CTA owns an x-y tile of TX x TY columns and marches along z over a
+// chunk of planes.  Two shared-memory rings follow the march:
+//   raw  (3 planes, tile + 2-cell halo): cell type and fixed-point rest
+//        populations, the reference of every arrived population;
+//   den  (3 planes, tile + 1-cell halo): rest populations, drho, type and
+//        global index of the current time level, the source of the density
+//        stencils (gradients, Atwood number, Eq. 4 Hessian) and of the push
+//        targets.
+// With lead plane L the pipeline per iteration is
+//   phase 0  raw plane L+1 from HBM
+//   phase 1  drho of the den region at plane L (own slots from HBM/L2, source
+//            rest populations from the raw ring)
+//   phase 3  forces + collision of the tile at plane L-1 (own slots again,
+//            from L2), push of the new populations into the neighbours' slots.
+// All per-cell arithmetic is shared with the two-launch path
+// (lbm_cell.cuh), so both give identical states.
+#pragma once
+
+#include "lbm_cell.cuh"
+
+namespace lbm {
+
+struct RawCell {
+    int f0A, f0B, type, pad;
+};
+struct DenCell {
+    int f0A, f0B;
+    float drA, drB;
+};
+struct DenMeta {
+    int type, gidx;
+};
+
+template <int TX, int TY>
+struct Tiles {
+    static constexpr int NT = TX * TY;
+    static constexpr int RX = TX + 4, RY = TY + 4, RN = RX * RY;
+    static constexpr int DX = TX + 2, DY = TY + 2, DN = DX * DY;
+    static constexpr size_t smem()
+    {
+        return 3 * RN * sizeof(RawCell) + 3 * DN * (sizeof(DenCell) + sizeof(DenMeta) + sizeof(float));
+    }
+};
+
+__device__ __forceinline__ int wrap_coord(int v, int n, int per)
+{
+    if (v >= 0 && v < n) return v;
+    if (!per) return -1;
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+__device__ __forceinline__ int ring3(int p) { return ((p % 3) + 3) % 3; }
+
+// One work item: the TX x TY columns at (x0, y0) over planes [za, zb) of the
+// lattice of shape G (G.n is the slot stride of ly, type, gray and macro),
+// physics P.  Ends with a block barrier, so the rings can be reused at once.
+template <int TX, int TY, bool MACRO, class LY>
+__device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, const LY &ly,
+                                           const uint8_t *__restrict__ type,
+                                           GrayRec *__restrict__ gray, float *__restrict__ macro, int x0, int y0,
+                                           int za, int zb, unsigned char *smem_raw)
+{
+    using T = Tiles<TX, TY>;
+    RawCell *raw = reinterpret_cast<RawCell *>(smem_raw);         // [3][RN]
+    DenCell *den = reinterpret_cast<DenCell *>(raw + 3 * T::RN);  // [3][DN]
+    DenMeta *dmeta = reinterpret_cast<DenMeta *>(den + 3 * T::DN); // [3][DN]
+    float *dat = reinterpret_cast<float *>(dmeta + 3 * T::DN);     // [3][DN] Atwood number
+    const int n = G.n;
+    const int tid = threadIdx.x;
+
+    // ---- phase 0: raw plane q (tile + 2-cell halo) ----
+    auto load_raw = [&](int q) {
+        const int gz = wrap_coord(q, G.nz, P.per[2]);
+        RawCell *dst = raw + ring3(q) * T::RN;
+        for (int e = tid; e < T::RN; e += T::NT) {
+            const int rx = e % T::RX, ry = e / T::RX;
+            const int gx = wrap_coord(x0 - 2 + rx, G.nx, P.per[0]);
+            const int gy = wrap_coord(y0 - 2 + ry, G.ny, P.per[1]);
+            RawCell rc = {0, 0, CELL_SOLID, 0};
+            if (gx >= 0 && gy >= 0 && gz >= 0) {
+                const int g = gx + G.nx * (gy + G.ny * gz);
+                rc.type = type[g];
+                if (rc.type != CELL_SOLID) {
+                    rc.f0A = ly.rest_in(0, g);
+                    rc.f0B = ly.rest_in(1, g);
+                }
+            }
+            dst[e] = rc;
+        }
+    };
+
+    // ---- phase 1: drho of the den region (tile + 1-cell halo) at plane L ----
+    auto densities = [&](int L) {
+        const RawCell *r0 = raw + ring3(L - 1) * T::RN;
+        const RawCell *r1 = raw + ring3(L) * T::RN;
+        const RawCell *r2 = raw + ring3(L + 1) * T::RN;
+        DenCell *dd = den + ring3(L) * T::DN;
+        DenMeta *dm = dmeta + ring3(L) * T::DN;
+        float *da = dat + ring3(L) * T::DN;
+        const int gz = wrap_coord(L, G.nz, P.per[2]);
+        for (int e = tid; e < T::DN; e += T::NT) {
+            const int dx = e % T::DX, dy = e / T::DX;
+            const RawCell me = r1[(dx + 1) + T::RX * (dy + 1)];
+            DenCell dc = {me.f0A, me.f0B, 0.f, 0.f};
+            int g = -1;
+            if (me.type != CELL_SOLID) {
+                g = wrap_coord(x0 - 1 + dx, G.nx, P.per[0]) +
+                    G.nx * (wrap_coord(y0 - 1 + dy, G.ny, P.per[1]) + G.ny * gz);
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const int f0 = a ? me.f0B : me.f0A;
+                    float acc = 0.f;
+                    long long id = 0;
+#pragma unroll
+                    for (int i = 1; i < Q; ++i) {
+                        const int o = opp(i);  // the source x - c_i is x + c_o
+                        const RawCell *rp = cz(o) < 0 ? r0 : (cz(o) > 0 ? r2 : r1);
+                        const RawCell &src = rp[(dx + 1 + cx(o)) + T::RX * (dy + 1 + cy(o))];
+                        acc += ly.mov_in(a, i, g);
+                        if (src.type != CELL_SOLID) id += (long long)((a ? src.f0B : src.f0A) - f0) * w12(i);
+                    }
+                    const float v = ff_add_f(ff_twelfth(id), acc).hi;
+                    if (a) dc.drB = v; else dc.drA = v;
+                }
+            }
+            dd[e] = dc;
+            dm[e] = {me.type, g};
+            da[e] = me.type != CELL_SOLID ? atwood_of(P.wet, dc.f0A, dc.f0B, dc.drA, dc.drB) : P.at_wall;
+        }
+    };
+
+    // ---- phase 3: forces + collision of the tile at plane z ----
+    auto collide = [&](int z) {
+        const int ux = tid % TX, uy = tid / TX;
+        if (x0 + ux >= G.nx || y0 + uy >= G.ny) return;
+        const DenCell *d0p = den + ring3(z - 1) * T::DN;
+        const DenCell *d1 = den + ring3(z) * T::DN;
+        const DenCell *d2 = den + ring3(z + 1) * T::DN;
+        const DenMeta *m0 = dmeta + ring3(z - 1) * T::DN;
+        const DenMeta *m1 = dmeta + ring3(z) * T::DN;
+        const DenMeta *m2 = dmeta + ring3(z + 1) * T::DN;
+        const float *a0 = dat + ring3(z - 1) * T::DN;
+        const float *a1 = dat + ring3(z) * T::DN;
+        const float *a2 = dat + ring3(z + 1) * T::DN;
+        const int dk = (ux + 1) + T::DX * (uy + 1);
+        const DenMeta me = m1[dk];
+        if (me.type == CELL_SOLID) {
+            if (MACRO) {
+                const int gc = (x0 + ux) + G.nx * ((y0 + uy) + G.ny * z);
+                for (int q = 0; q < 6; ++q) macro[(size_t)q * n + gc] = 0.0f;
+            }
+            return;
+        }
+        const int c = me.gidx;
+        const DenCell dc = d1[dk];
+        unsigned wall = 0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const DenMeta &nm = (cz(i) < 0 ? m0 : (cz(i) > 0 ? m2 : m1))[dk + cx(i) + T::DX * cy(i)];
+            if (nm.type == CELL_SOLID) wall |= 1u << i;
+        }
+        const int f0i[2] = {dc.f0A, dc.f0B};
+        CompMom M[2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            PullSums p;
+            pull_zero(p);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const int o = opp(i);  // the source x - c_i is x + c_o
+                int dfi = 0;
+                if (!(wall & (1u << o))) {
+                    const DenCell &sd = (cz(o) < 0 ? d0p : (cz(o) > 0 ? d2 : d1))[dk + cx(o) + T::DX * cy(o)];
+                    dfi = (a ? sd.f0B : sd.f0A) - f0i[a];
+                }
+                pull_add(p, i, ly.mov_in(a, i, c), dfi);
+            }
+            M[a] = finish_moments(p, f0i[a]);
+        }
+        const float r[2] = {M[0].rho.hi, M[1].rho.hi};
+        const uint8_t t = (uint8_t)me.type;
+        const bool is_gray = (t == CELL_GRAY);
+        const bool csf = P.kappa != 0.0f && (P.csf_everywhere || is_gray);
+        float gf[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, gAt[3] = {0.f, 0.f, 0.f};
+        HessSum hA, hB;
+        hess_zero(hA);
+        hess_zero(hB);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const DenCell &nd = (cz(i) < 0 ? d0p : (cz(i) > 0 ? d2 : d1))[dk + cx(i) + T::DX * cy(i)];
+            const bool wl = wall & (1u << i);
+            const float eA = wl ? P.rho_wall[0] - r[0] : nd.drA - dc.drA;
+            const float eB = wl ? P.rho_wall[1] - r[1] : nd.drB - dc.drB;
+            stencil_add(i, eA, eB, gf);
+            if (is_gray) atwood_add(i, (cz(i) < 0 ? a0 : (cz(i) > 0 ? a2 : a1))[dk + cx(i) + T::DX * cy(i)], gAt);
+            if (csf) {
+                const float dA = wl ? eA : 3.0f * fix_diff(nd.f0A, f0i[0]) + eA;
+                const float dB = wl ? eB : 3.0f * fix_diff(nd.f0B, f0i[1]) + eB;
+                hess_add(hA, i, dA);
+                hess_add(hB, i, dB);
+            }
+        }
+        auto tgt = [&](int i) -> size_t {
+            if (wall & (1u << i)) return (size_t)opp(i) * n + c;
+            const DenMeta &tm = (cz(i) < 0 ? m0 : (cz(i) > 0 ? m2 : m1))[dk + cx(i) + T::DX * cy(i)];
+            return (size_t)i * n + tm.gidx;
+        };
+        StoreRest<LY> st{ly, c, {f0i[0], f0i[1]}};
+        collide_store<MACRO>(P, G.accel, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
+    };
+
+    load_raw(za - 2);
+    load_raw(za - 1);
+    for (int L = za - 1; L <= zb; ++L) {
+        load_raw(L + 1);
+        __syncthreads();
+        densities(L);
+        __syncthreads();
+        if (L - 1 >= za) collide(L - 1);
+    }
+    __syncthreads();
+}
+
+}  // namespace lbm

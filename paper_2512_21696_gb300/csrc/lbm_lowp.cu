@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                 return (size_t)i * n + (cz(i) < 0 ? g0 : (cz(i) > 0 ? g2 : g1))[dk + cx(i) + T::DX * cy(i)];
             };
             StoreLP<H> st{fout, n, c, {r[0] * (1.0f / 3.0f), r[1] * (1.0f / 3.0f)}, {P.rho0[0], P.rho0[1]}, {0.f, 0.f}};
-            collide_store<MACRO>(P, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
+            collide_store<MACRO>(P, P.accel, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
         };
 
         densities(za - 1);

@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(256) k_collide(DevParams P, const float *__res
         return (wall & (1u << i)) ? (size_t)opp(i) * n + c : (size_t)i * n + nb[i];
     };
     StoreRest<LayF32> st{LayF32{fin, fout, n}, c, {f0i[0], f0i[1]}};
-    collide_store<MACRO>(P, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
+    collide_store<MACRO>(P, P.accel, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
 }
 
 // ---------------------------------------------------------------------------

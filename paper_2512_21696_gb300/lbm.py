@@ -52,6 +52,9 @@ class LbmContext:
         self._keep = []
 
     def close(self):
+        if getattr(self, "_view_of", None) is not None:  # a batch run: owned by its batch
+            self.handle = C.c_void_p(None)
+            return
         if self.handle and self.handle.value:
             L.load().lbm_destroy(self.handle)
             self.handle = C.c_void_p(None)
@@ -274,3 +277,63 @@ def lbm_observables_noalloc(fields, cell_type, phi, shape, G, probe, stream=None
         raise LbmError(code, "lbm_observables_noalloc")
     return dict(mass=(o.mass[0], o.mass[1]), sat=o.sat, flux_out=o.flux_out,
                 flux_vol=tuple(o.flux_vol), max_u=o.max_u, dp=o.dp, nan_count=o.nan_count, step=o.step)
+
+
+# ---------------------------------------------------------------- batches
+class LbmBatch:
+    """Owning handle of a batch of lattices (``lbm_batch_destroy`` on close)."""
+
+    def __init__(self, handle: int, runs):
+        self.handle = C.c_void_p(handle)
+        self.runs = list(runs)
+
+    def close(self):
+        if self.handle and self.handle.value:
+            L.load().lbm_batch_destroy(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def lbm_batch_create(runs) -> LbmBatch:
+    arr = (lbm_params * len(runs))(*runs)
+    h = C.c_void_p()
+    _check(L.load().lbm_batch_create(C.byref(h), len(runs), arr), "lbm_batch_create")
+    return LbmBatch(h.value, runs)
+
+
+def lbm_batch_run(batch: LbmBatch, run: int) -> LbmContext:
+    """The context of one run (a view of the batch's buffers)."""
+    h = C.c_void_p()
+    _check(L.load().lbm_batch_run(batch.handle, int(run), C.byref(h)), "lbm_batch_run")
+    ctx = LbmContext(h.value, batch.runs[run])
+    ctx._view_of = batch
+    return ctx
+
+
+def lbm_batch_step(batch: LbmBatch, nsteps: int) -> None:
+    _check(L.load().lbm_batch_step(batch.handle, int(nsteps)), "lbm_batch_step")
+
+
+def lbm_batch_tune(batch: LbmBatch, trial_steps: int = 10):
+    tiles = (C.c_int * len(batch.runs))()
+    _check(L.load().lbm_batch_tune(batch.handle, int(trial_steps), tiles), "lbm_batch_tune")
+    return list(tiles)
+
+
+def lbm_batch_info(batch: LbmBatch) -> dict:
+    cells, steps, launches = C.c_longlong(), C.c_longlong(), C.c_longlong()
+    groups = C.c_int()
+    _check(L.load().lbm_batch_info(batch.handle, C.byref(cells), C.byref(steps), C.byref(launches),
+                                   C.byref(groups)), "lbm_batch_info")
+    return dict(cells=cells.value, steps=steps.value, launches=launches.value, groups=groups.value)

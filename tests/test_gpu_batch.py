@@ -1,0 +1,136 @@
+"""Batched lattices (REV runs of uneven size in one persistent launch per step,
+replayed from CUDA graphs): each run must advance exactly like the same
+lattice alone, and like the FP64 oracle."""
+import numpy as np
+import pytest
+
+import lbm_cases as LC
+from helpers import rel_l2
+from paper_2512_21696_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+SHAPES = [(8, 8, 8), (9, 6, 11), (13, 17, 5), (20, 37, 35), (3, 3, 3)]
+
+
+def _cases():
+    out = []
+    for k, shp in enumerate(SHAPES):
+        c = LC.mixed_features(shape=shp, seed=40 + k)
+        # a different body acceleration per run
+        c.s["accel"] = ((1e-4 * (k + 1), 2e-5, 0.0), (0.0, -1e-4, 3e-5 * k))
+        out.append(c)
+    return out
+
+
+def _setup(ctx, case):
+    from paper_2512_21696_gb300 import lbm
+    for k, cv in enumerate(case.curves):
+        lbm.lbm_set_constitutive(ctx, k, lbm.lbm_default_constitutive(
+            kc_d=cv["kc_d"], pd=cv["pd"], lam=cv["lam"], swr=cv["swr"], nw=cv["nw"], nn=cv["nn"],
+            phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"]))
+    lbm.lbm_set_geometry(ctx, case.cell, case.phi32, case.ptype)
+    lbm.lbm_init_fields(ctx, case.rhoA32, case.rhoB32, case.u32)
+
+
+def _batch(cases, storage=0):
+    from paper_2512_21696_gb300 import lbm
+    b = lbm.lbm_batch_create([LC.gpu_params(c, storage=storage) for c in cases])
+    views = [lbm.lbm_batch_run(b, r) for r in range(len(cases))]
+    for v, c in zip(views, cases):
+        _setup(v, c)
+    return b, views
+
+
+def _close(a, b, tol):
+    for x, y in zip(a, b):
+        scale = max(1.0, float(np.abs(y).max()))
+        np.testing.assert_allclose(x, y, rtol=0, atol=tol * scale)
+
+
+@pytest.mark.parametrize("storage", [0, 3])
+def test_batch_runs_match_single_lattices_and_oracle(storage):
+    from paper_2512_21696_gb300 import lbm
+    cases = _cases()
+    b, views = _batch(cases, storage)
+    try:
+        lbm.lbm_batch_step(b, 12)
+        got = [[x.copy() for x in lbm.lbm_get_fields(v)] for v in views]
+        info = lbm.lbm_batch_info(b)
+        assert info["steps"] == 12 and info["cells"] == sum(int(np.prod(s)) for s in SHAPES)
+        assert info["launches"] == 12 * info["groups"]
+    finally:
+        b.close()
+    for case, g in zip(cases, got):
+        alone, _, _ = LC.run_gpu(case, 12, storage=storage, tile=2)
+        _close(g, alone, 1e-6)
+        if storage == 0:
+            of, _, _ = LC.run_oracle(case, 12)
+            fl = case.cell != synth.SOLID
+            for k, (x, y) in enumerate(zip(g, of)):
+                assert rel_l2(x, y, fl) <= 1e-5, (case.name, k)
+
+
+def test_batch_graph_replay_and_split_steps_agree():
+    from paper_2512_21696_gb300 import lbm
+    cases = _cases()
+    res = []
+    for split in (False, True):
+        b, views = _batch(cases)
+        try:
+            if split:
+                for _ in range(4):
+                    lbm.lbm_batch_step(b, 2)
+                lbm.lbm_batch_step(b, 2)  # replays the cached graph
+            else:
+                lbm.lbm_batch_step(b, 10)
+            res.append([[x.copy() for x in lbm.lbm_get_fields(v)] for v in views])
+            assert all(lbm.lbm_observables(v)["step"] == 10 for v in views)
+        finally:
+            b.close()
+    for x, y in zip(*res):
+        _close(x, y, 1e-6)
+
+
+def test_batch_tune_keeps_state():
+    from paper_2512_21696_gb300 import lbm
+    cases = _cases()
+    b, views = _batch(cases)
+    try:
+        lbm.lbm_batch_step(b, 3)
+        before = [[x.copy() for x in lbm.lbm_get_fields(v)] for v in views]
+        state = [lbm.lbm_save_state(v) for v in views]
+        tiles = lbm.lbm_batch_tune(b, 4)
+        assert len(tiles) == len(cases) and all(t in (0, 1, 2) for t in tiles)
+        after = [[x.copy() for x in lbm.lbm_get_fields(v)] for v in views]
+        for x, y in zip(before, after):
+            for p, q in zip(x, y):
+                np.testing.assert_array_equal(p, q)
+        assert [lbm.lbm_save_state(v) for v in views] == state
+        lbm.lbm_batch_step(b, 5)
+        got = [[x.copy() for x in lbm.lbm_get_fields(v)] for v in views]
+    finally:
+        b.close()
+    for case, g in zip(cases, got):
+        alone, _, _ = LC.run_gpu(case, 8, tile=2)
+        _close(g, alone, 1e-6)
+
+
+def test_batch_view_rules():
+    from paper_2512_21696_gb300 import lbm
+    cases = _cases()[:2]
+    b, views = _batch(cases)
+    try:
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_batch_run(b, 2)
+        assert L_destroy(views[0]) == -1
+        lbm.lbm_step(views[0], 1)  # one run alone: the parities now differ
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_batch_step(b, 1)
+        assert e.value.code == -6
+    finally:
+        b.close()
+
+
+def L_destroy(ctx):
+    from paper_2512_21696_gb300 import _lib
+    return _lib.load().lbm_destroy(ctx.handle)

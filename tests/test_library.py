@@ -72,3 +72,21 @@ def test_null_handles_are_rejected():
     assert lib.lbm_step(None, 1) == -1
     assert lib.lbm_destroy(None) == 0
     assert lib.lbm_observables(None, None) == -1
+
+
+def test_batch_create_rejects_mixed_physics_and_16bit_shift():
+    """Checked before any device work, so this runs without a GPU."""
+    import ctypes as C
+    from paper_2512_21696_gb300 import _lib, lbm
+    lib = _lib.load()
+    a = lbm.lbm_default_params(8, 8, 8)
+    b = lbm.lbm_default_params(12, 8, 8)
+    b.G = a.G + 0.1
+    arr = (lbm.lbm_params * 2)(a, b)
+    h = C.c_void_p()
+    assert lib.lbm_batch_create(C.byref(h), 2, arr) == -1
+    assert lib.lbm_batch_create(C.byref(h), 0, arr) == -1
+    c = lbm.lbm_default_params(8, 8, 8, storage=1)
+    arr1 = (lbm.lbm_params * 1)(c)
+    assert lib.lbm_batch_create(C.byref(h), 1, arr1) == -1
+    assert lib.lbm_batch_destroy(None) == 0
