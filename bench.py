@@ -418,6 +418,59 @@ def run_rev(args):
     print(json.dumps(out), flush=True)
 
 
+# --------------------------------------------------------- porosity gradient
+def run_adjoint(args):
+    """dL/dphi of the outlet-flux/saturation loss on the 96^3 multiscale-rock
+    recipe (A driven by the body force), hand-written adjoint with checkpoints
+    every --ckpt steps, against the forward alone."""
+    import torch
+    from paper_2512_21696_gb300 import lbm
+    torch.cuda.set_device(0)
+    inp = workload_inputs(96)
+    cell = inp["cell"]
+    nz, ny, nx = cell.shape
+    stream = torch.cuda.current_stream()
+    p = lbm.lbm_default_params(nx, ny, nz, stream=stream.cuda_stream, **SETTINGS)
+    ctx = lbm.lbm_create(p)
+    lbm.lbm_set_constitutive(ctx, 0, lbm.lbm_default_constitutive())
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in inp.items()}
+    lbm.lbm_set_geometry(ctx, dev["cell"], dev["phi"], dev["ptype"])
+    lbm.lbm_init_fields(ctx, dev["rhoA"], dev["rhoB"])
+    lbm.lbm_step(ctx, args.warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lbm.lbm_init_fields(ctx, dev["rhoA"], dev["rhoB"])
+    ev0.record(stream)
+    lbm.lbm_step(ctx, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_fwd = ev0.elapsed_time(ev1)
+    obs = lbm.lbm_observables(ctx, check=False)
+    q_t, s_t = 0.5 * obs["flux_out"] if obs["flux_out"] != 0 else 1e-6, obs["sat"] - 0.02
+    lbm.lbm_init_fields(ctx, dev["rhoA"], dev["rhoB"])
+    grad = torch.empty(cell.shape, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L, q, S, _ = lbm.lbm_adjoint_run(ctx, q_t, s_t, args.steps, args.ckpt, grad)
+    torch.cuda.synchronize()
+    ms_adj = (time.perf_counter() - t0) * 1e3
+    g = grad.cpu().numpy()
+    ctx.close()
+    n = cell.size
+    out = {"metric": METRIC, "value": round(n * args.steps / (ms_adj * 1e-3) / 1e6, 2), "unit": "MLUPS",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_adj / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded multiscale-rock recipe)",
+           "config": {"workload": f"porosity gradient (forward + checkpointed adjoint), 96^3 multiscale rock, "
+                                  f"{args.steps} steps, checkpoint every {args.ckpt}",
+                      "cells": n, "gray_cells": int((cell == 2).sum())},
+           "forward_ms": round(ms_fwd, 3), "forward_plus_adjoint_ms": round(ms_adj, 3),
+           "adjoint_over_forward": round(ms_adj / ms_fwd, 2),
+           "loss": {"L": L, "q": q, "S": S, "q_target": q_t, "s_target": s_t},
+           "grad": {"max_abs": float(np.abs(g).max()), "nonzero": int(np.count_nonzero(g))}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,8 +482,10 @@ def main():
     ap.add_argument("--path", type=int, default=0, help="0 fused single launch, 1 two launches")
     ap.add_argument("--storage", choices=list(STORAGE_IDS), default="f32",
                     help="population storage: f32; f16 / bf16 globally shifted; f16r / bf16r rest-referenced (FP32 arithmetic)")
-    ap.add_argument("--workload", choices=("drainage", "rev"), default="drainage",
-                    help="drainage: the 128^3 multiscale-rock step; rev: the batched REV library")
+    ap.add_argument("--workload", choices=("drainage", "rev", "adjoint"), default="drainage",
+                    help="drainage: the 128^3 multiscale-rock step; rev: the batched REV library; "
+                         "adjoint: the porosity gradient on the 96^3 recipe")
+    ap.add_argument("--ckpt", type=int, default=100, help="adjoint checkpoint interval")
     ap.add_argument("--rev-runs", type=int, default=256)
     ap.add_argument("--tile", type=int, default=2,
                     help="fused tile: 0 = 32x8, 1 = 32x16, 2 = 32x8 two CTAs/SM, 3 = 32x12, 4 = 64x8")
@@ -444,6 +499,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "rev":
         run_rev(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -249,6 +249,33 @@ LBM_API int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *c
  * LBM_ERR_ARG on unknown values. */
 LBM_API int lbm_set_kernel(lbm_ctx *ctx, int path, int tile);
 
+/* ---- Porosity gradient (discrete adjoint) ---------------------------------
+ * Loss on the fields of the last step (outlet flux and saturation mismatch):
+ *   L = (q - q_target)^2 / q_target^2 + (S - s_target)^2,
+ *   q = mean of u_x over the plane x = nx - 1 (solid cells count 0),
+ *   S = sum(phi_c Sw) / sum(phi_c) over non-solid cells (phi_c = 1 in pores). */
+typedef struct lbm_loss {
+    double q_target;  /* nonzero */
+    double s_target;
+} lbm_loss;
+
+/* Runs nsteps forward steps from the current state (F32 storage, not a batch
+ * run), evaluates L, and computes dL/dphi for every cell (0 outside gray
+ * cells) with the hand-written adjoint of the step: the forward keeps a
+ * checkpoint every ckpt steps; the backward recomputes each segment from its
+ * checkpoint and runs the adjoint step backwards through it, then chains the
+ * gray-cell constants to phi through the geometry precompute (Kozeny-Carman
+ * K0, Leverett factor, residual crossings of Eq. 5 / Fig. 6, the principal
+ * axis of Eqs. 6-7 via d e1 = sum_{k != 1} e_k (e_k^T dM e1)/(mu1 - mu_k)).
+ * Piecewise-constant parts (residual hysteresis, the H(At) cut-off, clamps)
+ * contribute their active branch.  dL_dphi: n floats, host or device (mem).
+ * out3 (may be NULL): L, q, S.  Ends at the forward's final state (as
+ * lbm_step(nsteps) would).  Device memory: (nsteps/ckpt + ckpt + 5)
+ * population buffers.  Synchronous.  The paper does not differentiate its
+ * model; this is the calibration use of it. */
+LBM_API int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int ckpt, float *dL_dphi, int mem,
+                            double *out3);
+
 /* ---- Batches of lattices (REV library runs, workflow step ii) -----------
  * A batch advances many independent lattices of uneven size together: one
  * persistent launch per step (and tile shape in use) takes (run, column,

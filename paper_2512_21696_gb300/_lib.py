@@ -77,6 +77,10 @@ class lbm_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_longlong), ("total_ms", C.c_double)]
 
 
+class lbm_loss(C.Structure):
+    _fields_ = [("q_target", C.c_double), ("s_target", C.c_double)]
+
+
 EXPORTS = [
     "lbm_strerror", "lbm_last_cuda_error", "lbm_abi_version", "lbm_default_params",
     "lbm_default_constitutive", "lbm_create", "lbm_destroy", "lbm_set_constitutive",
@@ -84,6 +88,7 @@ EXPORTS = [
     "lbm_get_static", "lbm_state_size", "lbm_save_state", "lbm_load_state", "lbm_profile",
     "lbm_profile_read", "lbm_launch_count", "lbm_struct_size", "lbm_observables_noalloc", "lbm_set_kernel",
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_run", "lbm_batch_step", "lbm_batch_tune", "lbm_batch_info",
+    "lbm_adjoint_run",
 ]
 
 _lock = threading.Lock()
@@ -131,6 +136,8 @@ def load(build_if_needed: bool = True):
         lib.lbm_observables_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_double,
                                                 C.POINTER(C.c_double), vp, C.POINTER(lbm_obs)]
         lib.lbm_set_kernel.argtypes = [P, C.c_int, C.c_int]
+        lib.lbm_adjoint_run.argtypes = [P, C.POINTER(lbm_loss), C.c_int, C.c_int, vp, C.c_int,
+                                        C.POINTER(C.c_double)]
         lib.lbm_batch_create.argtypes = [C.POINTER(P), C.c_int, C.POINTER(lbm_params)]
         lib.lbm_batch_destroy.argtypes = [P]
         lib.lbm_batch_run.argtypes = [P, C.c_int, C.POINTER(P)]

@@ -337,3 +337,23 @@ def lbm_batch_info(batch: LbmBatch) -> dict:
     _check(L.load().lbm_batch_info(batch.handle, C.byref(cells), C.byref(steps), C.byref(launches),
                                    C.byref(groups)), "lbm_batch_info")
     return dict(cells=cells.value, steps=steps.value, launches=launches.value, groups=groups.value)
+
+
+# ------------------------------------------------------ porosity gradient
+def lbm_adjoint_run(ctx: LbmContext, q_target: float, s_target: float, nsteps: int, ckpt: int, out=None):
+    """(L, q, S, dL/dphi) after nsteps from the current state (see lbm.h).
+
+    out: optional float32 array (NumPy) or CUDA tensor of n cells receiving
+    dL/dphi; a NumPy array is returned when it is None."""
+    loss = L.lbm_loss(float(q_target), float(s_target))
+    res = (C.c_double * 3)()
+    if out is None:
+        out = np.empty(ctx.shape, np.float32)
+    if not _is_device(out) and (not isinstance(out, np.ndarray) or out.dtype != np.float32
+                                or not out.flags.c_contiguous):
+        raise TypeError("host output must be a C-contiguous float32 NumPy array")
+    keep = []
+    ptr = _ptr(out, np.float32, ctx.ncell, keep)
+    _check(L.load().lbm_adjoint_run(ctx.handle, C.byref(loss), int(nsteps), int(ckpt), ptr, _mem_kind([out]), res),
+           "lbm_adjoint_run")
+    return res[0], res[1], res[2], out

@@ -173,3 +173,19 @@ def fiber_flow(n=24, axis=0, seed=synth.SEED_BASE + 2, ncyl=12, aniso=10.0, g=1e
     return Case(f"fiber{n}_{'xyz'[axis]}", shape, cell, phi, np.full(shape, 0.03), np.full(shape, 1.0),
                 ptype=ptype, curves=[dict(CURVE, aniso=aniso)], G=1.1, accel=((0, 0, 0), tuple(acc)),
                 rho_wall=(0.03, 1.0), wet=1)
+
+
+def adjoint_case(n=8, seed=21, shape=None, steps_hint=None):
+    """Periodic lattice with solid, gray (one curve, tensorial, CSF, capillary)
+    and both components, for the porosity gradient: A pushed along x."""
+    rng = np.random.default_rng(seed)
+    shape = shape or (n, n, n)
+    cell = np.zeros(shape, np.uint8)
+    cell[rng.random(shape) < 0.10] = synth.SOLID
+    cell[(rng.random(shape) < 0.45) & (cell == 0)] = synth.GRAY
+    phi = np.where(cell == synth.GRAY, 0.2 + 0.5 * rng.random(shape), 1.0)
+    zz, yy, xx = np.meshgrid(*(np.arange(s) for s in shape), indexing="ij")
+    ra = np.where(xx < shape[2] // 2, 1.0, 0.03) + 0.02 * rng.random(shape)
+    rb = 1.05 - ra
+    return Case(f"adjoint{shape}", shape, cell, phi, ra, rb, curves=[dict(CURVE, aniso=10.0)], G=1.1,
+                kappa=-0.045, tau=(0.8, 1.0), accel=((1e-4, 0, 0), (0, 0, 0)), rho_wall=(0.03, 1.0), wet=1)

@@ -1,0 +1,118 @@
+"""The hand-written adjoint (lbm_adjoint_run) against the oracle's discrete
+adjoint, central differences of the FP32 forward, and itself under other
+checkpoint intervals; the autograd wrapper."""
+import numpy as np
+import pytest
+
+import lbm_cases as LC
+from paper_2512_21696_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TARGETS = (2e-3, 0.45)
+
+
+def _ctx(case):
+    from paper_2512_21696_gb300 import lbm
+    ctx = lbm.lbm_create(LC.gpu_params(case))
+    cv = case.curves[0]
+    lbm.lbm_set_constitutive(ctx, 0, lbm.lbm_default_constitutive(
+        kc_d=cv["kc_d"], pd=cv["pd"], lam=cv["lam"], swr=cv["swr"], nw=cv["nw"], nn=cv["nn"],
+        phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"]))
+    return ctx
+
+
+def _gpu_grad(case, steps, ckpt, phi=None):
+    from paper_2512_21696_gb300 import lbm
+    ctx = _ctx(case)
+    try:
+        lbm.lbm_set_geometry(ctx, case.cell, case.phi32 if phi is None else phi.astype(np.float32))
+        lbm.lbm_init_fields(ctx, case.rhoA32, case.rhoB32)
+        L, q, S, g = lbm.lbm_adjoint_run(ctx, *TARGETS, steps, ckpt)
+        fields = [x.copy() for x in lbm.lbm_get_fields(ctx)]
+    finally:
+        ctx.close()
+    return L, q, S, g, fields
+
+
+def _oracle_grad(case, steps):
+    from oracle import adjoint as A
+    return A.loss_and_gradient(case.s, case.cell, case.curves[0], case.phi32.astype(np.float64),
+                               case.rhoA32.astype(np.float64), case.rhoB32.astype(np.float64), steps, *TARGETS)
+
+
+@pytest.mark.parametrize("steps,ckpt", [(6, 4), (40, 16)])
+def test_adjoint_matches_oracle_discrete_adjoint(steps, ckpt):
+    case = LC.adjoint_case()
+    L, q, S, g, _ = _gpu_grad(case, steps, ckpt)
+    Lo, qo, So, go = _oracle_grad(case, steps)
+    gray = case.cell == synth.GRAY
+    err = np.linalg.norm((g - go)[gray]) / np.linalg.norm(go[gray])
+    print(f"steps {steps}: L {L:.6e} (oracle {Lo:.6e}), relative L2 gradient error {err:.3e}")
+    assert abs(L - Lo) <= 1e-5 * abs(Lo)
+    assert np.count_nonzero(g[~gray]) == 0
+    assert err <= 2e-3
+
+
+def test_adjoint_is_independent_of_the_checkpoint_interval():
+    case = LC.adjoint_case(seed=22)
+    _, _, _, g1, f1 = _gpu_grad(case, 24, 24)
+    _, _, _, g2, f2 = _gpu_grad(case, 24, 5)
+    gray = case.cell == synth.GRAY
+    # same recomputed states; the FP32 atomic sums of the neighbour adjoints
+    # add in a different order, which moves the result at the 1e-4 level
+    assert np.linalg.norm((g1 - g2)[gray]) <= 5e-4 * np.linalg.norm(g1[gray])
+    for x, y in zip(f1, f2):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_adjoint_matches_central_differences_of_the_fp32_forward():
+    from paper_2512_21696_gb300 import lbm
+    case = LC.adjoint_case(n=10, seed=23)
+    steps = 30
+    _, _, _, g, _ = _gpu_grad(case, steps, 10)
+    gray = np.argwhere(case.cell == synth.GRAY)
+    rng = np.random.default_rng(7)
+    h = 2e-3
+    scale = np.abs(g).max()
+    errs = []
+    for k in rng.choice(len(gray), 16, replace=False):
+        idx = tuple(gray[k])
+        Ls = []
+        for sgn in (1, -1):
+            phi = case.phi32.astype(np.float64).copy()
+            phi[idx] += sgn * h
+            ctx = _ctx(case)
+            try:
+                lbm.lbm_set_geometry(ctx, case.cell, phi.astype(np.float32))
+                lbm.lbm_init_fields(ctx, case.rhoA32, case.rhoB32)
+                lbm.lbm_step(ctx, steps)
+                o = lbm.lbm_observables(ctx)
+            finally:
+                ctx.close()
+            Ls.append((o["flux_out"] - TARGETS[0]) ** 2 / TARGETS[0] ** 2 + (o["sat"] - TARGETS[1]) ** 2)
+        fd = (Ls[0] - Ls[1]) / (2 * h)
+        errs.append(abs(fd - g[idx]) / scale)
+    print("max |fd - adjoint| / max|grad| =", max(errs))
+    assert max(errs) <= 0.02
+
+
+def test_autograd_function_and_final_state():
+    import torch
+    from paper_2512_21696_gb300 import adjoint, lbm
+    case = LC.adjoint_case(seed=24)
+    ctx = _ctx(case)
+    try:
+        phi = torch.tensor(case.phi32, requires_grad=True)
+        loss = adjoint.porosity_loss(phi, ctx, case.cell, case.rhoA32, case.rhoB32, nsteps=12, ckpt=5,
+                                     q_target=TARGETS[0], s_target=TARGETS[1])
+        loss.backward()
+        after = [x.copy() for x in lbm.lbm_get_fields(ctx)]
+    finally:
+        ctx.close()
+    L, q, S, g, _ = _gpu_grad(case, 12, 5)
+    assert abs(float(loss) - L) <= 1e-12 * abs(L)  # the forward is deterministic
+    gray = case.cell == synth.GRAY
+    assert np.linalg.norm((phi.grad.numpy() - g)[gray]) <= 5e-4 * np.linalg.norm(g[gray])
+    plain, _, _ = LC.run_gpu(case, 12)
+    for x, y in zip(after, plain):
+        np.testing.assert_array_equal(x, y)
