@@ -154,6 +154,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(inwin)}
 
 
+# ------------------------------------------------------------ aggregation
+def max_over_ranks(value, dist, device):
+    """Largest per-rank value: the job ends with its slowest rank."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(cells, steps, world, ms):
+    """Whole-job throughput: every rank advances its own replica of `cells`."""
+    return world * cells * steps / (ms * 1e-3) / 1e6
+
+
 # ----------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -201,10 +217,7 @@ def run_ours(args, rank, world, local_rank):
     prof = lbm.lbm_profile_read(ctx)
     lbm.lbm_profile(ctx, False)
     launches = lbm.lbm_launch_count(ctx) - launches0
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     obs = lbm.lbm_observables(ctx, check=False)
 
     # end-to-end through the public API with pinned host buffers
@@ -220,10 +233,7 @@ def run_ours(args, rank, world, local_rank):
     lbm.lbm_get_fields(ctx, *[o.numpy() for o in outs])
     obs_e2e = lbm.lbm_observables(ctx, check=False)
     e_ms = (time.perf_counter() - e0) * 1e3
-    if dist:
-        t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
+    e_ms = max_over_ranks(e_ms, dist, "cuda")
     clocks.stop()
     ctx.close()
 
@@ -232,7 +242,7 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
     alg, fluid, gray = algorithmic_bytes(cell)
-    mlups = world * n * args.steps / (ms * 1e-3) / 1e6
+    mlups = job_mlups(n, args.steps, world, ms)
     dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("k_collide", (args.steps, ms))
     dname, (dlaunch, dtotal) = dom
     avg_s = dtotal / max(dlaunch, 1) * 1e-3
@@ -260,7 +270,7 @@ def run_ours(args, rank, world, local_rank):
         "step_roofline": {"alg_bytes_per_cell": round(alg[step_key] / n, 2), "achieved_gbs": round(step_gbs, 1),
                           "frac": round(step_gbs / peak, 4)},
         "kernels": {k: {"launches": v[0], "avg_ms": round(v[1] / max(v[0], 1), 5)} for k, v in prof.items()},
-        "e2e": {"value": round(world * n * args.steps / (e_ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+        "e2e": {"value": round(job_mlups(n, args.steps, world, e_ms), 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "ms_total": round(e_ms, 3)},
         "gpu_launches": launches,
