@@ -50,6 +50,21 @@ SETTINGS = dict(G=1.1, kappa_csf=-0.045, body_accel=((1e-5, 0.0, 0.0), (0.0, 0.0
                 wet_idx=1)
 
 
+def fiber_inputs(edge=192, axis=0):
+    """Tensorial-resistivity fibre bundle: 400 seeded cylinders (r = 1.5, vMF
+    kappa = 20 axes), gray where phi < 0.99, no solid; wetting B at rho_hi
+    everywhere with A dissolved, body force 1e-5 on B along `axis`."""
+    from paper_2512_21696_gb300 import synth
+    cell, phi, ptype, _ = synth.fiber_bundle_geometry(edge, synth.SEED_BASE + 3)
+    acc = [0.0, 0.0, 0.0]
+    acc[axis] = 1e-5
+    inp = dict(cell=cell, phi=phi.astype(np.float32), ptype=ptype,
+               rhoA=np.full(cell.shape, 0.03, np.float32), rhoB=np.full(cell.shape, 1.0, np.float32))
+    settings = dict(G=1.1, kappa_csf=-0.045, body_accel=((0.0, 0.0, 0.0), tuple(acc)), rho_wall=(0.03, 1.0),
+                    wet_idx=1)
+    return inp, settings, dict(aniso=10.0)
+
+
 def algorithmic_bytes(cell):
     """Bytes each kernel must move per launch (per-cell figures)."""
     n = cell.size
@@ -179,15 +194,20 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    inp = workload_inputs()
+    if args.workload == "fiber":
+        inp, settings, constitutive = fiber_inputs()
+        workload = ("tensorial fibre bundle, 192^3, 400 cylinders, anisotropy 10, body force on B along x, "
+                    "2-component D3Q19, FP32")
+    else:
+        inp, settings, constitutive, workload = workload_inputs(), SETTINGS, {}, WORKLOAD
     cell = inp["cell"]
     nz, ny, nx = cell.shape
     n = cell.size
     stream = torch.cuda.current_stream()
-    p = lbm.lbm_default_params(nx, ny, nz, stream=stream.cuda_stream, storage=STORAGE_IDS[args.storage], **SETTINGS)
+    p = lbm.lbm_default_params(nx, ny, nz, stream=stream.cuda_stream, storage=STORAGE_IDS[args.storage], **settings)
     ctx = lbm.lbm_create(p)
     lbm.lbm_set_kernel(ctx, args.path, args.tile)
-    lbm.lbm_set_constitutive(ctx, 0, lbm.lbm_default_constitutive())
+    lbm.lbm_set_constitutive(ctx, 0, lbm.lbm_default_constitutive(**constitutive))
     dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in inp.items()}
     lbm.lbm_set_geometry(ctx, dev["cell"], dev["phi"], dev["ptype"])
     lbm.lbm_init_fields(ctx, dev["rhoA"], dev["rhoB"])
@@ -257,7 +277,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded multiscale-rock recipe)",
-        "config": {"workload": WORKLOAD if args.storage == "f32" else WORKLOAD.replace("FP32", f"{args.storage.upper()} shifted storage, FP32 arithmetic"),
+        "config": {"workload": workload if args.storage == "f32" else workload.replace("FP32", f"{args.storage.upper()} storage, FP32 arithmetic"),
                    "storage": args.storage, "cells": n, "fluid_frac": round(fluid / n, 4),
                    "gray_frac": round(gray / n, 4), "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (2 x 319 MB population buffers)",
@@ -278,7 +298,10 @@ def run_ours(args, rank, world, local_rank):
         "observables": {"mass": obs["mass"], "sat": obs["sat"], "nan_count": obs["nan_count"],
                         "e2e_nan_count": obs_e2e["nan_count"]},
     }
-    if world == 1 and not args.no_cpu_baseline:
+    if args.workload == "fiber":
+        # Darcy: K_x = <u_x> nu / g over all cells (tau = 1), at the step reached
+        out["permeability_x_at_step"] = {"K": obs["flux_vol"][0] * (0.5 / 3.0) / 1e-5, "step": obs["step"]}
+    if world == 1 and not args.no_cpu_baseline and args.workload == "drainage":
         out["cpu_baseline"] = cpu_baseline(inp, budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
     if dist:
@@ -428,6 +451,44 @@ def run_rev(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------ static droplet
+def run_droplet(args):
+    """32^3 static droplet (R = 8, rho 1.0/0.03, G = 1.1, tau = 1): the state
+    fits in L2, so the step is launch-bound; it runs as a one-lattice batch,
+    whose steps are replayed from a CUDA graph.  Reported as us per step."""
+    import torch
+    from paper_2512_21696_gb300 import lbm, synth
+    torch.cuda.set_device(0)
+    shape = (32, 32, 32)
+    rA, rB = synth.droplet_fields(shape, 8, (16, 16, 16), 1.0, 0.03)
+    stream = torch.cuda.current_stream()
+    p = lbm.lbm_default_params(32, 32, 32, stream=stream.cuda_stream, G=1.1, probe_center=(16.0, 16.0, 16.0),
+                               probe_r_in=4.0, probe_r_out=12.0, storage=STORAGE_IDS[args.storage])
+    b = lbm.lbm_batch_create([p])
+    v = lbm.lbm_batch_run(b, 0)
+    lbm.lbm_set_geometry(v, np.zeros(shape, np.uint8), np.ones(shape, np.float32))
+    lbm.lbm_init_fields(v, rA.astype(np.float32), rB.astype(np.float32))
+    steps = args.steps + (args.steps & 1)
+    lbm.lbm_batch_step(b, steps)  # capture + warm-up
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lbm.lbm_batch_step(b, steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    o = lbm.lbm_observables(v, check=False)
+    b.close()
+    out = {"metric": METRIC, "value": round(32 ** 3 * steps / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+           "n_gpus": 1, "steps": steps, "warmup": steps, "ms_per_step": ms / steps, "us_per_step": 1e3 * ms / steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (droplet)",
+           "config": {"workload": "static droplet 32^3, R = 8, G = 1.1, tau = 1 (fits in L2: launch-bound)",
+                      "storage": args.storage, "graph": True},
+           "observables": {"mass": o["mass"], "dp": o["dp"], "max_u": o["max_u"], "step": o["step"]}}
+    print(json.dumps(out), flush=True)
+
+
 # --------------------------------------------------------- porosity gradient
 def run_adjoint(args):
     """dL/dphi of the outlet-flux/saturation loss on the 96^3 multiscale-rock
@@ -492,8 +553,9 @@ def main():
     ap.add_argument("--path", type=int, default=0, help="0 fused single launch, 1 two launches")
     ap.add_argument("--storage", choices=list(STORAGE_IDS), default="f32",
                     help="population storage: f32; f16 / bf16 globally shifted; f16r / bf16r rest-referenced (FP32 arithmetic)")
-    ap.add_argument("--workload", choices=("drainage", "rev", "adjoint"), default="drainage",
-                    help="drainage: the 128^3 multiscale-rock step; rev: the batched REV library; "
+    ap.add_argument("--workload", choices=("drainage", "fiber", "droplet", "rev", "adjoint"), default="drainage",
+                    help="drainage: the 128^3 multiscale-rock step; fiber: the 192^3 tensorial fibre bundle; "
+                         "droplet: the 32^3 static droplet (CUDA-graph replay); rev: the batched REV library; "
                          "adjoint: the porosity gradient on the 96^3 recipe")
     ap.add_argument("--ckpt", type=int, default=100, help="adjoint checkpoint interval")
     ap.add_argument("--rev-runs", type=int, default=256)
@@ -511,6 +573,8 @@ def main():
         run_rev(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload == "droplet":
+        run_droplet(args)
     else:
         run_ours(args, rank, world, local_rank)
 

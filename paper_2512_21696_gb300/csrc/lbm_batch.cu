@@ -147,8 +147,9 @@ void free_graphs(lbm_batch *b)
     b->graphs.clear();
 }
 
-// Work items of one run for a tile shape: columns x z-chunks of about 16 planes.
-lbm::BatchRun describe_run(const lbm_batch *b, int r, const TileShape &ts)
+// Work items of one run for a tile shape: columns x z-chunks of `planes`
+// planes (the z-march amortises its two halo planes over them).
+lbm::BatchRun describe_run(const lbm_batch *b, int r, const TileShape &ts, int planes)
 {
     const lbm_params &p = b->views[r]->p;
     lbm::BatchRun R{};
@@ -158,7 +159,7 @@ lbm::BatchRun describe_run(const lbm_batch *b, int r, const TileShape &ts)
     R.n = b->views[r]->n;
     R.tiles_x = (p.nx + ts.tx - 1) / ts.tx;
     R.ncol = R.tiles_x * ((p.ny + ts.ty - 1) / ts.ty);
-    R.zchunks = std::max(1, (p.nz + 8) / 16);
+    R.zchunks = std::max(1, (p.nz + planes / 2) / planes);
     R.cell_off = b->cell_off[r];
     R.pop_off = b->pop_off[r];
     for (int a = 0; a < 2; ++a)
@@ -179,19 +180,28 @@ int build_groups(lbm_batch *b, const std::vector<int> &subset, const std::vector
         g.tile = kv.first;
         g.runs = kv.second;
         std::sort(g.runs.begin(), g.runs.end(), [&](int x, int y) { return b->views[x]->n > b->views[y]->n; });
+        int slots = 0;
+        const int rc = slots_for(b, g.tile, &slots);
+        if (rc != LBM_OK) return rc;
+        // planes per item: up to 16, fewer when the group has too little work
+        // for about four items per resident CTA (small batches, small runs)
+        const TileShape &ts = BATCH_TILES[g.tile];
+        long long colplanes = 0;
+        for (int r : g.runs) {
+            const lbm_params &p = b->views[r]->p;
+            colplanes += (long long)((p.nx + ts.tx - 1) / ts.tx) * ((p.ny + ts.ty - 1) / ts.ty) * p.nz;
+        }
+        const int planes = (int)std::max(1LL, std::min(16LL, colplanes / (4LL * slots)));
         std::vector<lbm::BatchRun> host;
         int items = 0;
         for (int r : g.runs) {
-            lbm::BatchRun R = describe_run(b, r, BATCH_TILES[g.tile]);
+            lbm::BatchRun R = describe_run(b, r, ts, planes);
             R.item0 = items;
             items += R.ncol * R.zchunks;
             host.push_back(R);
         }
         g.nruns = (int)host.size();
         g.nitems = items;
-        int slots = 0;
-        const int rc = slots_for(b, g.tile, &slots);
-        if (rc != LBM_OK) return rc;
         g.grid = std::max(1, std::min(items, slots));
         LBM_CUDA(cudaMalloc(&g.d_runs, host.size() * sizeof(lbm::BatchRun)));
         LBM_CUDA(cudaMalloc(&g.counter, sizeof(unsigned int)));
