@@ -451,6 +451,93 @@ def run_rev(args):
     print(json.dumps(out), flush=True)
 
 
+def run_revlib(args):
+    """REV library generation (the workflow's step ii) on a subset: for each of
+    --rev-runs REVs (pore types round robin) one single-phase run and eight
+    two-phase runs at Sw = 0.2 ... 0.9, all in one batch.  In a periodic REV
+    each component's mass is conserved, so the saturation set at t = 0 holds;
+    both components feel the same acceleration g along x.  After --steps:
+    K = <u_x> nu / g (single phase), Kr_a = q_a / q_single with
+    q_a = <(rho_a/rho) u_x>, Pc = mean p of non-wetting-rich cells minus
+    mean p of wetting-rich cells, p = (rhoA + rhoB)/3 + G rhoA rhoB."""
+    import torch
+    from paper_2512_21696_gb300 import lbm, synth
+    torch.cuda.set_device(0)
+    seed = synth.SEED_BASE + 5
+    lib = rev_library(args.rev_runs, seed)
+    stream = torch.cuda.current_stream()
+    tau, g, G = 3 * 0.012 + 0.5, 1e-4, 1.1
+    sws = [0.2 + 0.1 * k for k in range(8)]
+    runs, inits = [], []
+    for r, (e, kind, cell, phi) in enumerate(lib):
+        for k, sw in enumerate([None] + sws):
+            runs.append(lbm.lbm_default_params(e, e, e, stream=stream.cuda_stream, G=G, tau=(tau, tau),
+                                               rho_wall=(0.03, 1.0), wet_idx=1,
+                                               body_accel=((g, 0, 0), (g, 0, 0)) if sw else ((0, 0, 0), (g, 0, 0))))
+            if sw is None:
+                rA, rB = np.full(cell.shape, 0.03), np.full(cell.shape, 1.0)
+            else:
+                # wetting B on the lowest-ranked fraction sw of the pore cells of a smooth field
+                fld = synth.gaussian_random_field(cell.shape, max(2.0, e / 8.0), synth.rng_for(seed + 77 * r + k))
+                pore = cell != synth.SOLID
+                cut = np.quantile(fld[pore], sw)
+                wet = pore & (fld <= cut)
+                rA, rB = np.where(wet, 0.03, 1.0), np.where(wet, 1.0, 0.03)
+            inits.append((cell, phi, rA.astype(np.float32), rB.astype(np.float32)))
+    b = lbm.lbm_batch_create(runs)
+    views = [lbm.lbm_batch_run(b, r) for r in range(len(runs))]
+    for v, (cell, phi, rA, rB) in zip(views, inits):
+        lbm.lbm_set_geometry(v, cell, phi.astype(np.float32))
+        lbm.lbm_init_fields(v, rA, rB)
+    cells = sum(int(np.prod(c.shape)) for c, _, _, _ in inits)
+    tiles = lbm.lbm_batch_tune(b, 6)
+    steps = args.steps + (args.steps & 1)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lbm.lbm_batch_step(b, steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    nu = (tau - 0.5) / 3.0
+    curves = {}
+    for r, (e, kind, cell, phi) in enumerate(lib):
+        base = r * 9
+        ra, rb, u, swf = lbm.lbm_get_fields(views[base])
+        q1 = float(u[0].mean())
+        ent = curves.setdefault(kind, dict(K=[], Sw=[], Krw=[], Krn=[], Pc=[]))
+        ent["K"].append(q1 * nu / g)
+        row = dict(Sw=[], Krw=[], Krn=[], Pc=[])
+        for k in range(8):
+            ra, rb, u, swf = lbm.lbm_get_fields(views[base + 1 + k])
+            pore = cell != synth.SOLID
+            rt = np.where(pore, ra + rb, 1.0)
+            qw, qn = float((rb / rt * u[0])[pore].sum() / cell.size), float((ra / rt * u[0])[pore].sum() / cell.size)
+            p = (ra + rb) / 3.0 + G * ra * rb
+            nrich, wrich = pore & (ra > rb), pore & (rb > ra)
+            row["Sw"].append(float(swf[pore].mean()))
+            row["Krw"].append(qw / q1 if q1 else np.nan)
+            row["Krn"].append(qn / q1 if q1 else np.nan)
+            row["Pc"].append(float(p[nrich].mean() - p[wrich].mean()) if nrich.any() and wrich.any() else np.nan)
+        for key in row:
+            ent[key].append(row[key])
+    b.close()
+    def avg(rows, nd):
+        with np.errstate(all="ignore"):
+            m = np.nanmean(np.asarray(rows, dtype=np.float64), axis=0)
+        return [round(float(x), nd) if np.isfinite(x) else None for x in np.atleast_1d(m)]
+
+    summary = {kind: {"K": avg(v["K"], 6)[0], "Sw": avg(v["Sw"], 3), "Krw": avg(v["Krw"], 4),
+                      "Krn": avg(v["Krn"], 4), "Pc": avg(v["Pc"], 6)} for kind, v in curves.items()}
+    out = {"metric": METRIC, "value": round(cells * steps / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS", "n_gpus": 1,
+           "steps": steps, "warmup": 0, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded REV pore types)",
+           "config": {"workload": f"REV library: {len(lib)} REVs x (single phase + 8 saturations) = {len(runs)} "
+                                  "runs in one batch", "cells": cells, "storage": "f32"},
+           "tiles": {t: tiles.count(t) for t in sorted(set(tiles))}, "library_at_step": summary}
+    print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------ static droplet
 def run_droplet(args):
     """32^3 static droplet (R = 8, rho 1.0/0.03, G = 1.1, tau = 1): the state
@@ -553,9 +640,11 @@ def main():
     ap.add_argument("--path", type=int, default=0, help="0 fused single launch, 1 two launches")
     ap.add_argument("--storage", choices=list(STORAGE_IDS), default="f32",
                     help="population storage: f32; f16 / bf16 globally shifted; f16r / bf16r rest-referenced (FP32 arithmetic)")
-    ap.add_argument("--workload", choices=("drainage", "fiber", "droplet", "rev", "adjoint"), default="drainage",
+    ap.add_argument("--workload", choices=("drainage", "fiber", "droplet", "rev", "revlib", "adjoint"),
+                    default="drainage",
                     help="drainage: the 128^3 multiscale-rock step; fiber: the 192^3 tensorial fibre bundle; "
                          "droplet: the 32^3 static droplet (CUDA-graph replay); rev: the batched REV library; "
+                         "revlib: K, Kr and Pc at 8 saturations for a REV subset; "
                          "adjoint: the porosity gradient on the 96^3 recipe")
     ap.add_argument("--ckpt", type=int, default=100, help="adjoint checkpoint interval")
     ap.add_argument("--rev-runs", type=int, default=256)
@@ -575,6 +664,8 @@ def main():
         run_adjoint(args)
     elif args.workload == "droplet":
         run_droplet(args)
+    elif args.workload == "revlib":
+        run_revlib(args)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -100,12 +100,16 @@ __device__ __forceinline__ void pull_zero(PullSums &p)
 }
 // Adds direction i: g = g_i at the source (or the bounce-back value), d0 the
 // rest-population difference f_0(s) - f_0(x) in fixed point (0 at walls).
+// WITH_D = false skips the zeroth moment (when the density pass already has it).
+template <bool WITH_D = true>
 __device__ __forceinline__ void pull_add(PullSums &p, int i, float g, int d0)
 {
     const long long D = (long long)d0 * w12(i);
     const float h = fmaf(w3(i) * FIX_INV, (float)d0, g);
-    p.d += g;
-    p.Id += D;
+    if (WITH_D) {
+        p.d += g;
+        p.Id += D;
+    }
     if (cx(i)) { p.j0 += cx(i) * g; p.sxx += h; p.Ij0 += cx(i) * D; }
     if (cy(i)) { p.j1 += cy(i) * g; p.syy += h; p.Ij1 += cy(i) * D; }
     if (cz(i)) { p.j2 += cz(i) * g; p.szz += h; p.Ij2 += cz(i) * D; }
@@ -122,10 +126,14 @@ struct CompMom {
     float S[6];        // sum c c h: xx, yy, zz, xy, xz, yz (FP32)
     long long Ij[3];   // integer part of j, also gives grad(rho) below
 };
-__device__ __forceinline__ CompMom finish_moments(const PullSums &p, int f0)
+// rho - 3 f_0 in float-float from the sums of the pulled g and of the
+// weighted rest-population differences (the density pass's value).
+__device__ __forceinline__ ff density_dev(long long Id, float d) { return ff_add_f(ff_twelfth(Id), d); }
+
+// Moments from the pull sums; dff = rho - 3 f_0 as float-float.
+__device__ __forceinline__ CompMom finish_moments_d(const PullSums &p, int f0, ff dff)
 {
     CompMom m;
-    const ff dff = ff_add_f(ff_twelfth(p.Id), p.d);
     m.dr = dff.hi;
     m.rho = ff_add(ff_from_ll(3LL * f0, FIX_INV), dff);
     m.j[0] = ff_add_f(ff_twelfth(p.Ij0), p.j0);
@@ -141,6 +149,10 @@ __device__ __forceinline__ CompMom finish_moments(const PullSums &p, int f0)
     m.S[4] = p.sxz;
     m.S[5] = p.syz;
     return m;
+}
+__device__ __forceinline__ CompMom finish_moments(const PullSums &p, int f0)
+{
+    return finish_moments_d(p, f0, density_dev(p.Id, p.d));
 }
 
 // Accumulates the FP32 parts of grad(rho^a) (e = rho^a(x+c_i) - rho^a(x)

@@ -28,7 +28,8 @@ struct RawCell {
 };
 struct DenCell {
     int f0A, f0B;
-    float drA, drB;
+    float drA, drB;  // rho - 3 f_0 (hi) ...
+    float loA, loB;  // ... and its low part (float-float)
 };
 struct DenMeta {
     int type, gidx;
@@ -104,7 +105,7 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
         for (int e = tid; e < T::DN; e += T::NT) {
             const int dx = e % T::DX, dy = e / T::DX;
             const RawCell me = r1[(dx + 1) + T::RX * (dy + 1)];
-            DenCell dc = {me.f0A, me.f0B, 0.f, 0.f};
+            DenCell dc = {me.f0A, me.f0B, 0.f, 0.f, 0.f, 0.f};
             int g = -1;
             if (me.type != CELL_SOLID) {
                 g = wrap_coord(x0 - 1 + dx, G.nx, P.per[0]) +
@@ -122,8 +123,14 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
                         acc += ly.mov_in(a, i, g);
                         if (src.type != CELL_SOLID) id += (long long)((a ? src.f0B : src.f0A) - f0) * w12(i);
                     }
-                    const float v = ff_add_f(ff_twelfth(id), acc).hi;
-                    if (a) dc.drB = v; else dc.drA = v;
+                    const ff v = density_dev(id, acc);
+                    if (a) {
+                        dc.drB = v.hi;
+                        dc.loB = v.lo;
+                    } else {
+                        dc.drA = v.hi;
+                        dc.loA = v.lo;
+                    }
                 }
             }
             dd[e] = dc;
@@ -176,9 +183,9 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
                     const DenCell &sd = (cz(o) < 0 ? d0p : (cz(o) > 0 ? d2 : d1))[dk + cx(o) + T::DX * cy(o)];
                     dfi = (a ? sd.f0B : sd.f0A) - f0i[a];
                 }
-                pull_add(p, i, ly.mov_in(a, i, c), dfi);
+                pull_add<false>(p, i, ly.mov_in(a, i, c), dfi);
             }
-            M[a] = finish_moments(p, f0i[a]);
+            M[a] = finish_moments_d(p, f0i[a], a ? ff{dc.drB, dc.loB} : ff{dc.drA, dc.loA});
         }
         const float r[2] = {M[0].rho.hi, M[1].rho.hi};
         const uint8_t t = (uint8_t)me.type;
