@@ -284,9 +284,11 @@ def run_ours(args, rank, world, local_rank):
                    "kernels_per_step": round(launches / args.steps, 3)},
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": ncu_traffic(dname),
+                     "frac": round(achieved / peak, 4), "frac_of_nominal_8tbs": round(achieved / 8000.0, 4),
+                     "traffic": ncu_traffic(dname),
                      "alg_bytes_per_launch": alg.get(dkey, alg[step_key]),
                      "avg_launch_ms": round(avg_s * 1e3, 5)},
+        "mflups": round(job_mlups(fluid, args.steps, world, ms), 2),  # non-solid cells only
         "step_roofline": {"alg_bytes_per_cell": round(alg[step_key] / n, 2), "achieved_gbs": round(step_gbs, 1),
                           "frac": round(step_gbs / peak, 4)},
         "kernels": {k: {"launches": v[0], "avg_ms": round(v[1] / max(v[0], 1), 5)} for k, v in prof.items()},
