@@ -301,6 +301,9 @@ LBM_API int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int ckp
  *   2 = 32x16) and keeps the fastest; the state is restored afterwards.
  *   tiles_out (nruns entries, may be NULL) receives the choice per run.
  *   Synchronous.
+ * lbm_batch_observables: lbm_observables of every run into out[nruns]
+ *   (synchronous); LBM_ERR_NUMERIC if any run has non-finite fields, with
+ *   every entry filled.
  * lbm_batch_info: total cells, steps taken, kernels launched by
  *   lbm_batch_step, and the number of launches per step. */
 typedef struct lbm_batch lbm_batch;
@@ -310,6 +313,7 @@ LBM_API int lbm_batch_run(lbm_batch *b, int run, lbm_ctx **view);
 LBM_API int lbm_batch_step(lbm_batch *b, int nsteps);
 LBM_API int lbm_batch_tune(lbm_batch *b, int trial_steps, int *tiles_out);
 LBM_API int lbm_batch_info(lbm_batch *b, long long *cells, long long *steps, long long *launches, int *ngroups);
+LBM_API int lbm_batch_observables(lbm_batch *b, lbm_obs *out);
 
 /* Number of kernels the context has launched since creation. */
 LBM_API int lbm_launch_count(lbm_ctx *ctx, long long *count);

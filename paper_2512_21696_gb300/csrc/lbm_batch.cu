@@ -548,4 +548,16 @@ int lbm_batch_info(lbm_batch *b, long long *cells, long long *steps, long long *
     return LBM_OK;
 }
 
+int lbm_batch_observables(lbm_batch *b, lbm_obs *out)
+{
+    if (!b || !out) return LBM_ERR_ARG;
+    int worst = LBM_OK;
+    for (size_t r = 0; r < b->views.size(); ++r) {
+        const int rc = lbm_observables(b->views[r], &out[r]);
+        if (rc == LBM_ERR_NUMERIC) worst = LBM_ERR_NUMERIC;
+        else if (rc != LBM_OK) return rc;
+    }
+    return worst;
+}
+
 }  // extern "C"

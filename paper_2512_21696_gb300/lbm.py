@@ -331,6 +331,16 @@ def lbm_batch_tune(batch: LbmBatch, trial_steps: int = 10):
     return list(tiles)
 
 
+def lbm_batch_observables(batch: LbmBatch, check: bool = True) -> list:
+    """lbm_observables of every run (one dict per run)."""
+    arr = (L.lbm_obs * len(batch.runs))()
+    code = L.load().lbm_batch_observables(batch.handle, arr)
+    if code not in (L.LBM_OK, L.LBM_ERR_NUMERIC) or (check and code != L.LBM_OK):
+        raise LbmError(code, "lbm_batch_observables")
+    return [dict(mass=(o.mass[0], o.mass[1]), sat=o.sat, flux_out=o.flux_out, flux_vol=tuple(o.flux_vol),
+                 max_u=o.max_u, dp=o.dp, nan_count=o.nan_count, step=o.step) for o in arr]
+
+
 def lbm_batch_info(batch: LbmBatch) -> dict:
     cells, steps, launches = C.c_longlong(), C.c_longlong(), C.c_longlong()
     groups = C.c_int()

@@ -134,3 +134,16 @@ def test_batch_view_rules():
 def L_destroy(ctx):
     from paper_2512_21696_gb300 import _lib
     return _lib.load().lbm_destroy(ctx.handle)
+
+
+def test_batch_observables_equal_per_run_observables():
+    from paper_2512_21696_gb300 import lbm
+    cases = _cases()[:3]
+    b, views = _batch(cases)
+    try:
+        lbm.lbm_batch_step(b, 4)
+        allobs = lbm.lbm_batch_observables(b)
+        for v, o in zip(views, allobs):
+            assert lbm.lbm_observables(v) == o
+    finally:
+        b.close()

@@ -213,3 +213,33 @@ def test_fused_matches_two_launch_path(tile):
     b, _, _ = LC.run_gpu(case, 25, path=1)
     for x, y in zip(a, b):
         np.testing.assert_allclose(x, y, rtol=0, atol=2e-6 * max(1.0, np.abs(y).max()))
+
+
+def test_host_injected_faults_are_reported():
+    """Faults made on the host: a NaN porosity is rejected by the geometry
+    call; a NaN density in the initial fields is counted by the observables,
+    which then return LBM_ERR_NUMERIC (the context stays usable)."""
+    from paper_2512_21696_gb300 import lbm
+    case = LC.mixed_features(seed=9)
+    ctx = lbm.lbm_create(LC.gpu_params(case))
+    try:
+        badphi = case.phi32.copy()
+        badphi[case.cell == synth.GRAY] = np.nan
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_set_geometry(ctx, case.cell, badphi, case.ptype)
+        assert e.value.code == -1
+        lbm.lbm_set_geometry(ctx, case.cell, case.phi32, case.ptype)
+        ra = case.rhoA32.copy()
+        ra[case.cell != synth.SOLID] = np.where(np.arange((case.cell != synth.SOLID).sum()) == 3, np.nan,
+                                                ra[case.cell != synth.SOLID])
+        lbm.lbm_init_fields(ctx, ra, case.rhoB32, case.u32)
+        lbm.lbm_step(ctx, 2)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_observables(ctx)
+        assert e.value.code == -4
+        assert lbm.lbm_observables(ctx, check=False)["nan_count"] > 0
+        lbm.lbm_init_fields(ctx, case.rhoA32, case.rhoB32, case.u32)
+        lbm.lbm_step(ctx, 2)
+        assert lbm.lbm_observables(ctx)["nan_count"] == 0
+    finally:
+        ctx.close()
