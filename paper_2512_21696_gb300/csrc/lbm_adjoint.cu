@@ -62,7 +62,7 @@ __device__ __forceinline__ float cSc(int i, const float S[6])
            2.f * (cx(i) * cy(i) * S[3] + cx(i) * cz(i) * S[4] + cy(i) * cz(i) * S[5]);
 }
 
-__global__ void __launch_bounds__(128) k_adj_cell(DevParams P, const float *__restrict__ fin,
+__global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *__restrict__ fin,
                                                   const float *__restrict__ rhob, const uint8_t *__restrict__ type,
                                                   const float *__restrict__ phi, const GrayRec *__restrict__ gray,
                                                   const float *__restrict__ lam_next, float *__restrict__ lam_out,
