@@ -54,33 +54,37 @@ __global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs 
 #pragma unroll
     for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
     const int n = P.n;
+    float umax = 0.0f;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const uint8_t t = type[c];
         if (t == CELL_SOLID) continue;
-        const double ra = macro[c], rb = macro[(size_t)n + c];
-        const double u0 = macro[(size_t)2 * n + c], u1 = macro[(size_t)3 * n + c], u2 = macro[(size_t)4 * n + c];
-        const double sw = macro[(size_t)5 * n + c];
+        // per-cell terms in FP32 (products of FP32 fields, one rounding each),
+        // every sum in FP64; FP64 is a small fraction of the FP32 rate here
+        const float ra = macro[c], rb = macro[(size_t)n + c];
+        const float u0 = macro[(size_t)2 * n + c], u1 = macro[(size_t)3 * n + c], u2 = macro[(size_t)4 * n + c];
+        const float sw = macro[(size_t)5 * n + c];
         if (!isfinite(ra) || !isfinite(rb) || !isfinite(u0) || !isfinite(u1) || !isfinite(u2)) {
             acc[13] += 1.0;
             continue;
         }
         const int x = c % P.nx, y = (c / P.nx) % P.ny, z = c / (P.nx * P.ny);
-        acc[0] += ra;
-        acc[1] += rb;
-        const double phc = t == CELL_GRAY ? (double)phi[c] : 1.0;
-        acc[2] += phc * sw;
-        acc[3] += phc;
-        if (x == P.nx - 1) acc[4] += u0;
-        acc[5] += u0;
-        acc[6] += u1;
-        acc[7] += u2;
-        acc[8] = fmax(acc[8], sqrt(u0 * u0 + u1 * u1 + u2 * u2));
-        const double dx = x - O.cx, dy = y - O.cy, dz = z - O.cz;
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        const double pr = (ra + rb) / 3.0 + O.G * ra * rb;
-        if (r2 < O.rin2) { acc[9] += pr; acc[10] += 1.0; }
-        if (r2 > O.rout2) { acc[11] += pr; acc[12] += 1.0; }
+        acc[0] += (double)ra;
+        acc[1] += (double)rb;
+        const float phc = t == CELL_GRAY ? phi[c] : 1.0f;
+        acc[2] += (double)(phc * sw);
+        acc[3] += (double)phc;
+        if (x == P.nx - 1) acc[4] += (double)u0;
+        acc[5] += (double)u0;
+        acc[6] += (double)u1;
+        acc[7] += (double)u2;
+        umax = fmaxf(umax, sqrtf(u0 * u0 + u1 * u1 + u2 * u2));
+        const float dx = x - (float)O.cx, dy = y - (float)O.cy, dz = z - (float)O.cz;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float pr = (ra + rb) * (1.0f / 3.0f) + (float)O.G * ra * rb;
+        if (r2 < (float)O.rin2) { acc[9] += (double)pr; acc[10] += 1.0; }
+        if (r2 > (float)O.rout2) { acc[11] += (double)pr; acc[12] += 1.0; }
     }
+    acc[8] = (double)umax;
     block_reduce(acc, sh);
     if (threadIdx.x == 0)
         for (int k = 0; k < NOBS; ++k) partial[(size_t)blockIdx.x * NOBS + k] = acc[k];
