@@ -444,6 +444,18 @@ def run_rev(args):
         o = lbm.lbm_observables(v, check=False)
         kperm.setdefault(kind, []).append(o["flux_vol"][0] * nu / g)
         taken = o["step"]
+    steady = None
+    if args.steady_max > 0:
+        # continue every run to steady flow (mean velocity changing by at most
+        # 1e-5 of itself over 500 steps), untimed; K is then the Darcy value
+        t0 = time.time()
+        ok, done = lbm.lbm_batch_step_to_steady(b, 500, 1e-5, args.steady_max)
+        wall = time.time() - t0
+        ks = {}
+        for o, (e, kind, cell, phi) in zip(lbm.lbm_batch_observables(b), lib):
+            ks.setdefault(kind, []).append(o["flux_vol"][0] * nu / g)
+        steady = {"reached": bool(ok), "extra_steps": done, "wall_s": round(wall, 2),
+                  "K": {k: round(float(np.mean(v)), 6) for k, v in ks.items()}}
     b.close()
     mlups = cells * steps / (ms_batch * 1e-3) / 1e6
     out = {"metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": 1, "steps": steps,
@@ -460,6 +472,8 @@ def run_rev(args):
            "tiles": {t: tiles.count(t) for t in sorted(set(tiles))}, "tune_s": round(tune_s, 2),
            "permeability_at_step": {k: round(float(np.mean(v)), 6) for k, v in kperm.items()},
            "steps_taken": taken}
+    if steady is not None:
+        out["steady_state"] = steady
     print(json.dumps(out), flush=True)
 
 
@@ -660,6 +674,8 @@ def main():
                          "adjoint: the porosity gradient on the 96^3 recipe")
     ap.add_argument("--ckpt", type=int, default=100, help="adjoint checkpoint interval")
     ap.add_argument("--rev-runs", type=int, default=256)
+    ap.add_argument("--steady-max", type=int, default=0,
+                    help="rev: after timing, step every run to steady flow (at most this many steps)")
     ap.add_argument("--tile", type=int, default=2,
                     help="fused tile: 0 = 32x8, 1 = 32x16, 2 = 32x8 two CTAs/SM, 3 = 32x12, 4 = 64x8")
     args = ap.parse_args()

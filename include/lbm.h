@@ -304,6 +304,12 @@ LBM_API int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int ckp
  * lbm_batch_observables: lbm_observables of every run into out[nruns]
  *   (synchronous); LBM_ERR_NUMERIC if any run has non-finite fields, with
  *   every entry filled.
+ * lbm_batch_step_to_steady: steps the batch check_every steps at a time
+ *   until, for every run, the mean velocity changed by at most rel_tol of its
+ *   largest component over the last chunk (steady flow: the permeability
+ *   K = <u> nu / g is then read at steady state), or until max_steps; returns
+ *   LBM_OK when steady, LBM_ERR_TIMEOUT when max_steps ran out; steps_done
+ *   (may be NULL) receives the steps taken.  Synchronous.
  * lbm_batch_info: total cells, steps taken, kernels launched by
  *   lbm_batch_step, and the number of launches per step. */
 typedef struct lbm_batch lbm_batch;
@@ -314,6 +320,7 @@ LBM_API int lbm_batch_step(lbm_batch *b, int nsteps);
 LBM_API int lbm_batch_tune(lbm_batch *b, int trial_steps, int *tiles_out);
 LBM_API int lbm_batch_info(lbm_batch *b, long long *cells, long long *steps, long long *launches, int *ngroups);
 LBM_API int lbm_batch_observables(lbm_batch *b, lbm_obs *out);
+LBM_API int lbm_batch_step_to_steady(lbm_batch *b, int check_every, double rel_tol, int max_steps, int *steps_done);
 
 /* Number of kernels the context has launched since creation. */
 LBM_API int lbm_launch_count(lbm_ctx *ctx, long long *count);

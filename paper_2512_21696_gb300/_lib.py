@@ -88,7 +88,7 @@ EXPORTS = [
     "lbm_get_static", "lbm_state_size", "lbm_save_state", "lbm_load_state", "lbm_profile",
     "lbm_profile_read", "lbm_launch_count", "lbm_struct_size", "lbm_observables_noalloc", "lbm_set_kernel",
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_run", "lbm_batch_step", "lbm_batch_tune", "lbm_batch_info",
-    "lbm_adjoint_run", "lbm_batch_observables",
+    "lbm_adjoint_run", "lbm_batch_observables", "lbm_batch_step_to_steady",
 ]
 
 _lock = threading.Lock()
@@ -139,6 +139,7 @@ def load(build_if_needed: bool = True):
         lib.lbm_adjoint_run.argtypes = [P, C.POINTER(lbm_loss), C.c_int, C.c_int, vp, C.c_int,
                                         C.POINTER(C.c_double)]
         lib.lbm_batch_observables.argtypes = [P, C.POINTER(lbm_obs)]
+        lib.lbm_batch_step_to_steady.argtypes = [P, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int)]
         lib.lbm_batch_create.argtypes = [C.POINTER(P), C.c_int, C.POINTER(lbm_params)]
         lib.lbm_batch_destroy.argtypes = [P]
         lib.lbm_batch_run.argtypes = [P, C.c_int, C.POINTER(P)]

@@ -15,6 +15,7 @@
 // All per-cell arithmetic is the single-lattice kernel's (lbm_fused.cuh): a
 // run advanced in a batch is bit-identical to the run advanced alone.
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <new>
 #include <vector>
@@ -546,6 +547,39 @@ int lbm_batch_info(lbm_batch *b, long long *cells, long long *steps, long long *
     if (launches) *launches = b->launches;
     if (ngroups) *ngroups = b->groups_ok ? (int)b->groups.size() : 0;
     return LBM_OK;
+}
+
+int lbm_batch_step_to_steady(lbm_batch *b, int check_every, double rel_tol, int max_steps, int *steps_done)
+{
+    if (!b || check_every < 1 || !(rel_tol > 0.0) || max_steps < 0) return LBM_ERR_ARG;
+    const size_t nr = b->views.size();
+    std::vector<lbm_obs> prev(nr), cur(nr);
+    int rc = lbm_batch_observables(b, prev.data());
+    if (rc != LBM_OK) return rc;
+    int done = 0;
+    bool steady = false;
+    while (!steady && done < max_steps) {
+        const int k = std::min(check_every, max_steps - done);
+        rc = lbm_batch_step(b, k);
+        if (rc != LBM_OK) return rc;
+        done += k;
+        rc = lbm_batch_observables(b, cur.data());
+        if (rc != LBM_OK) return rc;
+        steady = true;
+        for (size_t r = 0; r < nr && steady; ++r)
+            for (int d = 0; d < 3; ++d) {
+                const double a = cur[r].flux_vol[d], p = prev[r].flux_vol[d];
+                const double scale = std::max({std::fabs(cur[r].flux_vol[0]), std::fabs(cur[r].flux_vol[1]),
+                                               std::fabs(cur[r].flux_vol[2]), 1e-300});
+                if (std::fabs(a - p) > rel_tol * scale) {
+                    steady = false;
+                    break;
+                }
+            }
+        prev.swap(cur);
+    }
+    if (steps_done) *steps_done = done;
+    return steady ? LBM_OK : LBM_ERR_TIMEOUT;
 }
 
 int lbm_batch_observables(lbm_batch *b, lbm_obs *out)

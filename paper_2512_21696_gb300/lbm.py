@@ -341,6 +341,16 @@ def lbm_batch_observables(batch: LbmBatch, check: bool = True) -> list:
                  max_u=o.max_u, dp=o.dp, nan_count=o.nan_count, step=o.step) for o in arr]
 
 
+def lbm_batch_step_to_steady(batch: LbmBatch, check_every: int, rel_tol: float, max_steps: int):
+    """(steady, steps taken): steps until every run's mean velocity settles."""
+    done = C.c_int()
+    code = L.load().lbm_batch_step_to_steady(batch.handle, int(check_every), float(rel_tol), int(max_steps),
+                                             C.byref(done))
+    if code not in (L.LBM_OK, L.LBM_ERR_TIMEOUT):
+        raise LbmError(code, "lbm_batch_step_to_steady")
+    return code == L.LBM_OK, done.value
+
+
 def lbm_batch_info(batch: LbmBatch) -> dict:
     cells, steps, launches = C.c_longlong(), C.c_longlong(), C.c_longlong()
     groups = C.c_int()

@@ -150,3 +150,28 @@ def test_batch_observables_equal_per_run_observables():
             assert lbm.lbm_observables(v) == o
     finally:
         b.close()
+
+
+def test_batch_steady_state_permeability_matches_oracle():
+    """Single-phase REVs stepped to steady flow in one batch; K = <u_x> nu / g
+    of each run against the FP64 oracle run for the same number of steps."""
+    from paper_2512_21696_gb300 import lbm
+    g, tau = 1e-4, 3 * 0.012 + 0.5
+    cases = []
+    for k, kind in enumerate(("spheres", "grf", "slits")):
+        cell, phi, _ = synth.rev_geometry(16, kind, synth.SEED_BASE + 900 + k)
+        cases.append(LC.Case(f"rev_{kind}", cell.shape, cell, phi, np.full(cell.shape, 0.03),
+                             np.full(cell.shape, 1.0), G=1.1, tau=(tau, tau), accel=((0, 0, 0), (g, 0, 0)),
+                             rho_wall=(0.03, 1.0), wet=1))
+    b, views = _batch(cases)
+    try:
+        steady, steps = lbm.lbm_batch_step_to_steady(b, 200, 1e-5, 40000)
+        assert steady and 0 < steps < 40000
+        ks = [o["flux_vol"][0] * ((tau - 0.5) / 3.0) / g for o in lbm.lbm_batch_observables(b)]
+    finally:
+        b.close()
+    for case, kg in zip(cases, ks):
+        _, oobs, _ = LC.run_oracle(case, steps)
+        ko = oobs["flux_vol"][0] * ((tau - 0.5) / 3.0) / g
+        print(f"{case.name}: K gpu {kg:.6e} oracle {ko:.6e} after {steps} steps")
+        assert ko > 0 and abs(kg - ko) <= 1e-4 * abs(ko)
