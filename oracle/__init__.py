@@ -43,6 +43,7 @@ class OrcParams(C.Structure):
         ("rho_hi", C.c_double), ("rho_lo", C.c_double),
         ("s_lo", C.c_double), ("s_hi", C.c_double), ("at_cut", C.c_double),
         ("eps_n", C.c_double), ("kr_min", C.c_double), ("c_g", C.c_double),
+        ("rho_in", C.c_double * 2), ("rho_out", C.c_double * 2),
     ]
 
 
@@ -83,6 +84,7 @@ def _load():
         lib.orc_static.argtypes = [P, dp, dp, dp, dp, dp, ip]
         lib.orc_observables.argtypes = [P, dp, dp]
         lib.orc_set_populations.argtypes = [P, dp]
+        lib.orc_set_pressure.argtypes = [P, dp, dp]
         lib.orc_get_populations.argtypes = [P, dp]
         lib.orc_set_residual.argtypes = [P, dp, dp, ip]
         lib.orc_get_residual.argtypes = [P, dp, dp, ip]
@@ -145,6 +147,10 @@ def make_params(shape, **kw) -> OrcParams:
     p.eps_n = kw.pop("eps_n", 1e-4 * rho_hi)
     p.kr_min = kw.pop("kr_min", 1e-6)
     p.c_g = kw.pop("c_g", 1.0)
+    rin = kw.pop("rho_in", (rho_hi, rho_lo))
+    rout = kw.pop("rho_out", (rho_hi, rho_lo))
+    for a in range(2):
+        p.rho_in[a], p.rho_out[a] = rin[a], rout[a]
     if kw:
         raise TypeError(f"unknown oracle parameters {sorted(kw)}")
     return p
@@ -236,6 +242,11 @@ class Oracle:
         return dict(mass=(out[0], out[1]), sat=out[2], flux_out=out[3],
                     flux_vol=(out[4], out[5], out[6]), max_u=out[7], dp=out[8],
                     nan_count=int(out[9]))
+
+    def set_pressure(self, rho_in, rho_out):
+        """Densities (A, B) held in the inlet and outlet cells from the next step."""
+        self.lib.orc_set_pressure(self._h, np.asarray(rho_in, dtype=np.float64),
+                                  np.asarray(rho_out, dtype=np.float64))
 
     def populations(self):
         f = np.zeros(38 * self.n)

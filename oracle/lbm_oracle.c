@@ -37,6 +37,16 @@
  *   - Constitutive curves: Kozeny-Carman K0(phi) (Appendix), Brooks-Corey
  *     Pc(Sw), Corey Kr(Sw).
  *
+ *   - Pressure boundaries (the imbibition set-ups of Sec. I and the Appendix:
+ *     a pressure difference between two boundaries of the domain, lowered in
+ *     steps).  Reading: inlet / outlet cells are reservoirs held at given
+ *     component densities at rest.  In every step such a cell takes its
+ *     prescribed densities as its moments (so the force stencils of its
+ *     neighbours see them), carries no force and no velocity, and leaves the
+ *     collision as the rest equilibrium of those densities, which then
+ *     streams into the domain.  The pressure of a reservoir is
+ *     p = cs^2 (rhoA + rhoB) + G rhoA rhoB.
+ *
  * Order inside one step: stream; moments at all cells; residual update;
  * density gradients at all cells; forces and velocity; collide.
  * Every force reads neighbour densities of the same time level.
@@ -51,7 +61,7 @@
 
 #define ORC_MAX_TYPES 16
 
-enum { PORE = 0, SOLID = 1, GRAY = 2 };
+enum { PORE = 0, SOLID = 1, GRAY = 2, INLET = 3, OUTLET = 4 };
 enum { T_SC = 0, T_CSF = 1, T_CAP = 2, T_DRAG = 3, T_BODY = 4, N_TERM = 5 };
 
 typedef struct {
@@ -68,6 +78,7 @@ typedef struct {
     int wet;
     double rho_hi, rho_lo;
     double s_lo, s_hi, at_cut, eps_n, kr_min, c_g;
+    double rho_in[2], rho_out[2]; /* densities held in inlet / outlet cells */
 } orc_params;
 
 typedef struct {
@@ -159,6 +170,13 @@ static double rho_seen(const orc_state *st, long m, int a)
 }
 
 static double phi_seen(const orc_state *st, long m) { return m < 0 ? 0.0 : st->phi[m]; }
+
+/* Prescribed density of component a in pressure cell c (inlet or outlet). */
+static int is_pressure(const orc_state *st, long c) { return st->type[c] == INLET || st->type[c] == OUTLET; }
+static double rho_held(const orc_state *st, long c, int a)
+{
+    return st->type[c] == INLET ? st->p.rho_in[a] : st->p.rho_out[a];
+}
 
 static double *alloc0(long count) { return (double *)calloc((size_t)count, sizeof(double)); }
 
@@ -457,7 +475,7 @@ orc_state *orc_create(const orc_params *p, const orc_curve *curves, int ncurve,
     for (long c = 0; c < n; ++c) st->ptype[c] = ptype ? ptype[c] : 0;
     st->phi = alloc0(n);
     for (long c = 0; c < n; ++c)
-        st->phi[c] = type[c] == PORE ? 1.0 : (type[c] == SOLID ? 0.0 : phi[c]);
+        st->phi[c] = type[c] == SOLID ? 0.0 : (type[c] == GRAY ? phi[c] : 1.0);
     st->K0 = alloc0(n); st->lamL = alloc0(n); st->swirr = alloc0(n); st->sores = alloc0(n);
     st->kinv = alloc0(9 * n); st->e1 = alloc0(3 * n);
     st->iso = (int *)calloc((size_t)n, sizeof(int));
@@ -523,6 +541,15 @@ void orc_init_fields(orc_state *st, const double *rhoA, const double *rhoB, cons
     st->steps = 0;
 }
 
+/* New reservoir densities, used from the next step on. */
+void orc_set_pressure(orc_state *st, const double rho_in[2], const double rho_out[2])
+{
+    for (int a = 0; a < 2; ++a) {
+        st->p.rho_in[a] = rho_in[a];
+        st->p.rho_out[a] = rho_out[a];
+    }
+}
+
 void orc_set_populations(orc_state *st, const double *f) { memcpy(st->f, f, sizeof(double) * 38 * (size_t)st->n); }
 void orc_get_populations(const orc_state *st, double *f) { memcpy(f, st->f, sizeof(double) * 38 * (size_t)st->n); }
 void orc_set_residual(orc_state *st, const double *Rw, const double *Ro, const int *wet)
@@ -564,9 +591,9 @@ static void one_step(orc_state *st)
                 r += v;
                 for (int d = 0; d < 3; ++d) jc[d] += CV[i][d] * v;
             }
-            st->rho[a][c] = r;
+            st->rho[a][c] = is_pressure(st, c) ? rho_held(st, c, a) : r;
         }
-        for (int d = 0; d < 3; ++d) st->j[d * n + c] = jc[d];
+        for (int d = 0; d < 3; ++d) st->j[d * n + c] = is_pressure(st, c) ? 0.0 : jc[d];
     }
 
     /* (3) residual components: hysteresis on the normalised wetting density */
@@ -613,7 +640,7 @@ static void one_step(orc_state *st)
         for (int t = 0; t < N_TERM; ++t)
             for (int a = 0; a < 2; ++a)
                 for (int d = 0; d < 3; ++d) st->term[t][a][d * n + c] = 0.0;
-        if (st->type[c] == SOLID) {
+        if (st->type[c] == SOLID || is_pressure(st, c)) {
             for (int d = 0; d < 3; ++d) st->u[d * n + c] = 0.0;
             for (int a = 0; a < 2; ++a)
                 for (int d = 0; d < 3; ++d) st->F[a][d * n + c] = 0.0;
@@ -720,6 +747,15 @@ static void one_step(orc_state *st)
     for (long c = 0; c < n; ++c) {
         if (st->type[c] == SOLID) continue;
         double uc[3] = {st->u[c], st->u[n + c], st->u[2 * n + c]};
+        if (is_pressure(st, c)) {
+            /* reservoir: the rest equilibrium of the held densities */
+            for (int a = 0; a < 2; ++a) {
+                double feq[19];
+                equilibrium(st->rho[a][c], uc, feq);
+                for (int i = 0; i < 19; ++i) st->f[((long)a * 19 + i) * n + c] = feq[i];
+            }
+            continue;
+        }
         for (int a = 0; a < 2; ++a) {
             double fin[19], fout[19], Fa[3];
             for (int i = 0; i < 19; ++i) fin[i] = st->fs[((long)a * 19 + i) * n + c];
@@ -771,7 +807,8 @@ void orc_static(const orc_state *st, double *kinv, double *K0, double *lamL, dou
 }
 
 /* Observables: out[0..1] mass of A and B; out[2] saturation
- * sum(phi_c Sw)/sum(phi_c) (phi_c = 1 in pore, phi in gray); out[3] mean
+ * sum(phi_c Sw)/sum(phi_c) (phi_c = 1 in pore, phi in gray, pressure cells
+ * left out); out[3] mean
  * u_x over the outlet plane x = nx-1; out[4..6] volume mean of u; out[7]
  * max |u|; out[8] mean pressure inside radius r_in minus outside r_out about
  * the probe centre, p = cs^2 (rhoA+rhoB) + G rhoA rhoB; out[9] count of
@@ -794,9 +831,11 @@ void orc_observables(const orc_state *st, const double probe[5], double out[10])
         }
         mass[0] += ra;
         mass[1] += rb;
-        double phc = st->type[c] == GRAY ? st->phi[c] : 1.0;
-        satn += phc * st->sw[c];
-        satd += phc;
+        if (!is_pressure(st, c)) {
+            double phc = st->type[c] == GRAY ? st->phi[c] : 1.0;
+            satn += phc * st->sw[c];
+            satd += phc;
+        }
         if (x == p->nx - 1) fout += u0;
         fv[0] += u0; fv[1] += u1; fv[2] += u2;
         double um = sqrt(u0 * u0 + u1 * u1 + u2 * u2);

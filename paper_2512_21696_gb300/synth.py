@@ -17,7 +17,7 @@ from __future__ import annotations
 
 import numpy as np
 
-PORE, SOLID, GRAY = 0, 1, 2
+PORE, SOLID, GRAY, INLET, OUTLET = 0, 1, 2, 3, 4
 
 # Base seed of the synthetic workloads; workload k uses SEED_BASE + k.
 SEED_BASE = 2512216960

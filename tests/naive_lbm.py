@@ -11,14 +11,15 @@ the results.
 
 Equations: Eq. 2-3 (LB equation, force term), Eq. 4 (CSF), Eq. 1 (capillary
 and viscous multiscale force), Eq. 5 and Fig. 6 (Leverett scaling, residual
-components), Eq. 6-7 (tensorial resistivity); see the oracle's header for the
-readings of the points the paper leaves open.
+components), Eq. 6-7 (tensorial resistivity), and the reservoir reading of
+the pressure boundaries of the imbibition set-ups (Sec. I, Appendix); see the
+oracle's header for the readings of the points the paper leaves open.
 """
 from __future__ import annotations
 
 import numpy as np
 
-PORE, SOLID, GRAY = 0, 1, 2
+PORE, SOLID, GRAY, INLET, OUTLET = 0, 1, 2, 3, 4
 
 _VEL = [(0, 0, 0)]
 for d in range(3):
@@ -78,7 +79,7 @@ def kozeny_carman(d, phi):
 
 def geometry(cell, phi_in, curve, c_g=1.0):
     """Gray-cell constants: K^-1 (3x3 per cell), Leverett factor, residual bounds."""
-    phi = np.where(cell == PORE, 1.0, np.where(cell == SOLID, 0.0, phi_in)).astype(np.float64)
+    phi = np.where(cell == SOLID, 0.0, np.where(cell == GRAY, phi_in, 1.0)).astype(np.float64)
     g = iso_grad(phi)
     H = np.zeros((3, 3) + phi.shape)
     for a in range(3):
@@ -158,6 +159,7 @@ class NaiveLBM:
         self.cell = np.asarray(cell, dtype=np.uint8)
         self.solid = self.cell == SOLID
         self.gray = self.cell == GRAY
+        self.pres = (self.cell == INLET) | (self.cell == OUTLET)
         curve = curve or dict(kc_d=1.0, pd=0.02, **{"lambda": 2.0}, swr=0.15, nw=3.0, nn=2.0,
                               phi_ref=0.35, f_max=3.5, f_min=0.575, aniso=1.0)
         self.curve = curve
@@ -192,6 +194,11 @@ class NaiveLBM:
         fs = np.where(self.solid[None, None], 0.0, fs)
         rho = fs.sum(axis=1)
         j = np.tensordot(VEL.T.astype(dt), fs.sum(axis=0), axes=(1, 0))
+        # reservoirs: the held densities, no momentum
+        held = np.stack([np.where(self.cell == INLET, p.get("rho_in", (0, 0))[a], p.get("rho_out", (0, 0))[a])
+                         for a in range(2)]).astype(dt)
+        rho = np.where(self.pres[None], held, rho)
+        j = np.where(self.pres[None], 0.0, j)
         w = p["wet"]
         fluid = ~self.solid
         rt = np.where(fluid, rho[0] + rho[1], 1.0)
@@ -250,12 +257,16 @@ class NaiveLBM:
         ug = np.moveaxis(ug, -1, 0)
         un = (j + 0.5 * Fo) / rt[None]
         u = np.where(self.gray[None], ug, un)
-        u = np.where(self.solid[None], 0.0, u).astype(dt)
+        u = np.where((self.solid | self.pres)[None], 0.0, u).astype(dt)
         Ru = np.einsum("...ab,b...->a...", R, u)
         for a in range(2):
             terms[a]["drag"] = np.where(self.gray[None], -(rho[a] / rt)[None] * Ru, 0.0)
+            for k in terms[a]:
+                terms[a][k] = np.where(self.pres[None], 0.0, terms[a][k])
             F.append(sum(terms[a].values()))
         fnew = np.stack([collide(fs[a], u, F[a], p["tau"][a]) for a in range(2)])
+        rest = np.zeros((3,) + self.cell.shape, dt)
+        fnew = np.where(self.pres[None, None], np.stack([equilibrium(rho[a], rest) for a in range(2)]), fnew)
         self.f = np.where(self.solid[None, None], 0.0, fnew).astype(dt)
         self.rho, self.u, self.sw, self.terms = rho, u, sw, terms
         return self

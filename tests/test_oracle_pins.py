@@ -145,6 +145,40 @@ def test_darcy_uniform_gray(phi):
     np.testing.assert_allclose(ux, expected, rtol=1e-7)
 
 
+@pytest.mark.parametrize("phi", [0.6, 0.4])
+def test_darcy_between_pressure_reservoirs(phi):
+    """One component through a uniform gray column between an inlet and an
+    outlet reservoir (Eq. 1 drag, the reservoir reading of the pressure
+    boundaries).  At steady state the interior density is linear in x, the
+    mass flux rho u is the same at every cell and obeys Darcy's law
+    rho u = -(K0/nu) dp/dx with p = rho/3 and the local slope; the linear
+    profile reaches the held densities between the reservoir node and the
+    face half a cell beyond it (the same place as halfway bounce-back), and
+    the reservoirs keep their densities with u = 0."""
+    L = 16
+    shape = (1, 1, L)
+    cell = np.full(shape, synth.GRAY, np.uint8)
+    cell[..., 0], cell[..., -1] = synth.INLET, synth.OUTLET
+    r_in, r_out = 1.005, 0.995
+    p = O.make_params(shape, periodic=(0, 1, 1), wet=0, rho_in=(r_in, 0.0), rho_out=(r_out, 0.0))
+    o = O.Oracle(p, cell, np.full(shape, phi))
+    o.init_fields(np.ones(shape), np.zeros(shape))
+    o.step(60000)
+    a, b, u, sw = o.fields()
+    assert a[0, 0, 0] == r_in and a[0, 0, -1] == r_out and np.all(u[:, 0, 0, [0, -1]] == 0.0)
+    x = np.arange(1, L - 1)
+    r = a[0, 0, 1:-1]
+    slope, icpt = np.polyfit(x, r, 1)
+    assert np.abs(r - (slope * x + icpt)).max() < 1e-8 * abs(slope)
+    J = (a * u[0])[0, 0, 1:-1]
+    assert np.ptp(J) < 1e-8 * J.mean()
+    nu = 1.0 / 6.0
+    np.testing.assert_allclose(J.mean(), -kc(phi) / nu * slope / 3.0, rtol=1e-6)
+    x_in, x_out = (r_in - icpt) / slope, (r_out - icpt) / slope
+    assert 0.4 < x_in <= 0.5 and 0.4 < (L - 1) - x_out <= 0.5
+    assert abs(x_in - ((L - 1) - x_out)) < 1e-3  # the offset depends weakly on the local density
+
+
 def test_tensorial_resistivity_direction():
     """phi varying along z only puts the principal axis on z (Eq. 7).
 
@@ -468,13 +502,19 @@ def test_residual_hysteresis_switches():
 # --------------------------------------------------------------------------
 # Brute force: the C oracle against the independent NumPy evaluator
 # --------------------------------------------------------------------------
-def _bruteforce_case(seed, csf_everywhere, tau):
+def _bruteforce_case(seed, csf_everywhere, tau, pressure=False):
     rng = np.random.default_rng(seed)
     n = 8
     shape = (n, n, n)
     cell = np.zeros(shape, np.uint8)
     cell[rng.random(shape) < 0.12] = synth.SOLID
     cell[(rng.random(shape) < 0.35) & (cell == 0)] = synth.GRAY
+    bc = {}
+    if pressure:
+        # an inlet plane and an outlet plane (with holes of solid) inside the periodic box
+        cell[:, :, 0] = np.where(cell[:, :, 0] == synth.SOLID, synth.SOLID, synth.INLET)
+        cell[:, :, 4] = np.where(cell[:, :, 4] == synth.SOLID, synth.SOLID, synth.OUTLET)
+        bc = dict(rho_in=(0.08, 1.02), rho_out=(0.97, 0.05))
     phi = np.where(cell == synth.GRAY, 0.15 + 0.4 * rng.random(shape), 1.0)
     zz, yy, xx = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
     blocks = ((xx // 4 + yy // 4 + zz // 4) % 2) == 0
@@ -482,7 +522,7 @@ def _bruteforce_case(seed, csf_everywhere, tau):
     rb = 1.06 - ra
     u0 = 0.01 * rng.standard_normal((3,) + shape)
     common = dict(G=1.1, kappa=-0.045, tau=tau, accel=((1e-4, 2e-5, 0), (0, -1e-4, 3e-5)),
-                  c_g=1.0, rho_wall=(0.7, 0.2), wet=1, csf_everywhere=csf_everywhere)
+                  c_g=1.0, rho_wall=(0.7, 0.2), wet=1, csf_everywhere=csf_everywhere, **bc)
     curve = dict(kc_d=1.0, pd=0.02, swr=0.15, nw=3.0, nn=2.0, phi_ref=0.35, f_max=3.5,
                  f_min=0.575, aniso=10.0)
     o = O.Oracle(O.make_params(shape, **common), cell, phi, curves=[O.make_curve(lam=2.0, **curve)])
@@ -499,9 +539,10 @@ def _bruteforce_case(seed, csf_everywhere, tau):
     return o, nv, cell
 
 
-@pytest.mark.parametrize("csf_everywhere,tau", [(0, (0.8, 1.3)), (1, (1.0, 1.0))])
-def test_bruteforce_against_numpy_evaluator(csf_everywhere, tau):
-    o, nv, cell = _bruteforce_case(5, csf_everywhere, tau)
+@pytest.mark.parametrize("csf_everywhere,tau,pressure", [(0, (0.8, 1.3), False), (1, (1.0, 1.0), False),
+                                                         (0, (0.8, 1.3), True)])
+def test_bruteforce_against_numpy_evaluator(csf_everywhere, tau, pressure):
+    o, nv, cell = _bruteforce_case(5, csf_everywhere, tau, pressure)
     st = o.static()
     np.testing.assert_allclose(np.moveaxis(st["kinv"], (0, 1), (-2, -1)), nv.geo["kinv"],
                                rtol=1e-12, atol=0)
@@ -524,15 +565,17 @@ def test_bruteforce_against_numpy_evaluator(csf_everywhere, tau):
     np.testing.assert_allclose(o.populations(), nv.f, rtol=0, atol=1e-14)
 
 
-def test_observables_are_plain_sums():
-    o, nv, cell = _bruteforce_case(9, 0, (1.0, 1.0))
+@pytest.mark.parametrize("pressure", [False, True])
+def test_observables_are_plain_sums(pressure):
+    o, nv, cell = _bruteforce_case(9, 0, (1.0, 1.0), pressure)
     o.step(3)
     a, b, u, sw = o.fields()
     ob = o.observables(probe=(4, 4, 4, 2.5, 3.5))
     fl = cell != synth.SOLID
     assert abs(ob["mass"][0] - a[fl].sum()) < 1e-12
     phic = np.where(cell == synth.GRAY, o.static()["K0"] * 0 + nv.geo["phi"], 1.0)
-    assert abs(ob["sat"] - (phic * sw)[fl].sum() / phic[fl].sum()) < 1e-13
+    inner = fl & (cell != synth.INLET) & (cell != synth.OUTLET)  # saturation leaves reservoirs out
+    assert abs(ob["sat"] - (phic * sw)[inner].sum() / phic[inner].sum()) < 1e-13
     assert abs(ob["flux_out"] - u[0, :, :, -1].sum() / 64) < 1e-15
     assert abs(ob["max_u"] - np.sqrt((u ** 2).sum(axis=0))[fl].max()) < 1e-15
 
