@@ -22,7 +22,8 @@
  *     x + nx*(y + ny*z).  Per-cell arrays are dense in that order; vector
  *     fields are stored component-major, u[d*ncell + cell].
  *   - Cell types: LBM_CELL_PORE (resolved fluid), LBM_CELL_SOLID,
- *     LBM_CELL_GRAY (under-resolved porous cell with porosity 0 < phi < 1).
+ *     LBM_CELL_GRAY (under-resolved porous cell with porosity 0 < phi < 1),
+ *     LBM_CELL_INLET / LBM_CELL_OUTLET (pressure reservoirs, lbm_set_pressure).
  *   - Every call returns LBM_OK (0) or a negative LBM_ERR_* code and never
  *     throws; lbm_strerror() turns a code into text.  After an error the
  *     context stays valid unless the code is LBM_ERR_CUDA from a sticky CUDA
@@ -69,7 +70,13 @@ enum lbm_status {
 
 enum lbm_mem { LBM_MEM_HOST = 0, LBM_MEM_DEVICE = 1 };
 
-enum lbm_cell { LBM_CELL_PORE = 0, LBM_CELL_SOLID = 1, LBM_CELL_GRAY = 2 };
+enum lbm_cell {
+    LBM_CELL_PORE = 0,
+    LBM_CELL_SOLID = 1,
+    LBM_CELL_GRAY = 2,
+    LBM_CELL_INLET = 3,  /* reservoir held at the inlet densities */
+    LBM_CELL_OUTLET = 4  /* reservoir held at the outlet densities */
+};
 
 /* Population storage.  F32: the rest population f_0 and the deviations
  * f_i - 3 w_i f_0 (i >= 1) of each cell, in FP32.  F16S / BF16S: the shifted
@@ -196,7 +203,8 @@ LBM_API int lbm_destroy(lbm_ctx *ctx);
 LBM_API int lbm_set_constitutive(lbm_ctx *ctx, int pore_type, const lbm_constitutive *c);
 
 /* Geometry: type[ncell] (enum lbm_cell), phi[ncell] porosity of gray cells
- * (values at pore/solid cells are ignored and taken as 1/0), pore_type[ncell]
+ * (values at other cells are ignored and taken as 1, 0 at solid cells),
+ * pore_type[ncell]
  * (may be NULL = all type 0).  Runs the FP64 geometry precompute on the
  * device: gradient and Hessian of phi, principal axis of
  * M = H H + c_g grad(phi) grad(phi)^T (Eqs. 6-7 and the abstract), K0,
@@ -214,6 +222,22 @@ LBM_API int lbm_init_fields(lbm_ctx *ctx, const float *rhoA, const float *rhoB, 
 /* Advance nsteps >= 0 time steps (asynchronous).  The fields read back by
  * lbm_get_fields / lbm_observables are those of the last step. */
 LBM_API int lbm_step(lbm_ctx *ctx, int nsteps);
+
+/* Pressure boundaries: the densities held in the LBM_CELL_INLET and
+ * LBM_CELL_OUTLET cells (the imbibition set-ups of Sec. I and of the
+ * Appendix drive the flow by a pressure difference between two boundaries
+ * and lower it in steps; the paper does not say how the boundary is
+ * imposed).  A reservoir cell holds the given component densities at rest:
+ * in every step it takes them as its moments, so that the force stencils of
+ * its neighbours see them, carries no force and no velocity, and leaves the
+ * collision as their rest equilibrium, which streams into the domain.  Its
+ * pressure is p = (rhoA + rhoB)/3 + G rhoA rhoB.
+ *   rho_in[2], rho_out[2]: host arrays, densities (A, B) of the inlet and of
+ *   the outlet cells, finite, >= 0 with a positive sum; copied.
+ * Takes effect from the next step (also for a run of a batch, whose next
+ * step re-reads its runs).  Until called both hold (rho_hi, rho_lo).
+ * LBM_ERR_ARG on a NULL pointer or invalid densities.  No device work. */
+LBM_API int lbm_set_pressure(lbm_ctx *ctx, const double rho_in[2], const double rho_out[2]);
 
 /* FP64 reductions of the current fields into *out (synchronises).
  * Returns LBM_ERR_NUMERIC when nan_count > 0 (out is still filled). */
@@ -271,7 +295,8 @@ typedef struct lbm_loss {
  * contribute their active branch.  dL_dphi: n floats, host or device (mem).
  * out3 (may be NULL): L, q, S.  Ends at the forward's final state (as
  * lbm_step(nsteps) would).  Device memory: (nsteps/ckpt + ckpt + 5)
- * population buffers.  Synchronous.  The paper does not differentiate its
+ * population buffers.  Synchronous.  LBM_ERR_ARG for a geometry with
+ * pressure (inlet / outlet) cells, which the adjoint step does not model.  The paper does not differentiate its
  * model; this is the calibration use of it. */
 LBM_API int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int ckpt, float *dL_dphi, int mem,
                             double *out3);

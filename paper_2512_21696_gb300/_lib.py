@@ -23,7 +23,7 @@ LBM_ERR_STATE = -6
 LBM_MEM_HOST = 0
 LBM_MEM_DEVICE = 1
 
-LBM_CELL_PORE, LBM_CELL_SOLID, LBM_CELL_GRAY = 0, 1, 2
+LBM_CELL_PORE, LBM_CELL_SOLID, LBM_CELL_GRAY, LBM_CELL_INLET, LBM_CELL_OUTLET = 0, 1, 2, 3, 4
 LBM_STORAGE_F32, LBM_STORAGE_F16S, LBM_STORAGE_BF16S = 0, 1, 2
 LBM_MAX_PORE_TYPES = 16
 
@@ -88,7 +88,7 @@ EXPORTS = [
     "lbm_get_static", "lbm_state_size", "lbm_save_state", "lbm_load_state", "lbm_profile",
     "lbm_profile_read", "lbm_launch_count", "lbm_struct_size", "lbm_observables_noalloc", "lbm_set_kernel",
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_run", "lbm_batch_step", "lbm_batch_tune", "lbm_batch_info",
-    "lbm_adjoint_run", "lbm_batch_observables", "lbm_batch_step_to_steady",
+    "lbm_adjoint_run", "lbm_batch_observables", "lbm_batch_step_to_steady", "lbm_set_pressure",
 ]
 
 _lock = threading.Lock()
@@ -136,6 +136,7 @@ def load(build_if_needed: bool = True):
         lib.lbm_observables_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_double,
                                                 C.POINTER(C.c_double), vp, C.POINTER(lbm_obs)]
         lib.lbm_set_kernel.argtypes = [P, C.c_int, C.c_int]
+        lib.lbm_set_pressure.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         lib.lbm_adjoint_run.argtypes = [P, C.POINTER(lbm_loss), C.c_int, C.c_int, vp, C.c_int,
                                         C.POINTER(C.c_double)]
         lib.lbm_batch_observables.argtypes = [P, C.POINTER(lbm_obs)]

@@ -78,6 +78,12 @@ void fill_device_params(lbm_ctx *ctx)
     d.eps_n = (float)p.eps_n;
     d.kr_min = (float)p.kr_min;
     d.rho0[0] = d.rho0[1] = (float)(0.5 * (p.rho_hi + p.rho_lo));
+    for (int side = 0; side < 2; ++side)
+        for (int a = 0; a < 2; ++a) {
+            const double v = ctx->rho_held[side][a];
+            d.held[side][a][0] = (float)v;
+            d.held[side][a][1] = (float)(v - (double)(float)v);
+        }
     d.storage = p.storage;
     {
         const double ww = p.rho_wall[p.wet_idx], wn = p.rho_wall[1 - p.wet_idx];
@@ -90,6 +96,14 @@ void fill_device_params(lbm_ctx *ctx)
         d.curve[k].neg_inv_lambda = (float)(-1.0 / c.lambda);
         d.curve[k].nw = (float)c.nw;
         d.curve[k].nn = (float)c.nn;
+    }
+}
+
+void default_held(lbm_ctx *ctx)
+{
+    for (int side = 0; side < 2; ++side) {
+        ctx->rho_held[side][0] = ctx->p.rho_hi;
+        ctx->rho_held[side][1] = ctx->p.rho_lo;
     }
 }
 
@@ -249,6 +263,7 @@ int lbm_create(lbm_ctx **out, const lbm_params *p)
         return cuda_fail(cudaGetLastError(), "cudaGetDevice");
     }
     for (int k = 0; k < LBM_MAX_PORE_TYPES; ++k) lbm_default_constitutive(&ctx->curves[k]);
+    default_held(ctx);
     fill_device_params(ctx);
     const size_t N = (size_t)n;
     cudaError_t e = cudaSuccess;
@@ -319,16 +334,19 @@ int lbm_set_geometry(lbm_ctx *ctx, const uint8_t *type, const float *phi, const 
         std::memcpy(hphi.data(), phi, N * sizeof(float));
         if (pore_type) std::memcpy(hp8.data(), pore_type, N);
     }
+    long long held = 0;
     for (size_t c = 0; c < N; ++c) {
         const uint8_t t = ht[c];
-        if (t > LBM_CELL_GRAY) return LBM_ERR_ARG;
+        if (t > LBM_CELL_OUTLET) return LBM_ERR_ARG;
         if (t == LBM_CELL_GRAY) {
             if (!(hphi[c] > 0.0f && hphi[c] < 1.0f)) return LBM_ERR_ARG;
         } else {
-            hphi[c] = t == LBM_CELL_PORE ? 1.0f : 0.0f;
+            hphi[c] = t == LBM_CELL_SOLID ? 0.0f : 1.0f;
         }
+        held += lbm::is_held(t) ? 1 : 0;
         if (pore_type && hp8[c] >= LBM_MAX_PORE_TYPES) return LBM_ERR_ARG;
     }
+    ctx->n_held = held;
     LBM_CUDA(cudaMemcpyAsync(ctx->type, ht.data(), N, cudaMemcpyHostToDevice, ctx->stream));
     LBM_CUDA(cudaMemcpyAsync(ctx->phi, hphi.data(), N * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     Staging pt;
@@ -344,6 +362,22 @@ int lbm_set_geometry(lbm_ctx *ctx, const uint8_t *type, const float *phi, const 
     LBM_CUDA(cudaStreamSynchronize(ctx->stream));
     ctx->has_geometry = true;
     ctx->has_fields = false;
+    return LBM_OK;
+}
+
+int lbm_set_pressure(lbm_ctx *ctx, const double rho_in[2], const double rho_out[2])
+{
+    if (!ctx || !rho_in || !rho_out) return LBM_ERR_ARG;
+    for (const double *r : {rho_in, rho_out}) {
+        if (!std::isfinite(r[0]) || !std::isfinite(r[1]) || r[0] < 0.0 || r[1] < 0.0 || !(r[0] + r[1] > 0.0))
+            return LBM_ERR_ARG;
+    }
+    for (int a = 0; a < 2; ++a) {
+        ctx->rho_held[0][a] = rho_in[a];
+        ctx->rho_held[1][a] = rho_out[a];
+    }
+    fill_device_params(ctx);
+    if (ctx->owner) lbm::batch_runs_changed(ctx->owner);
     return LBM_OK;
 }
 

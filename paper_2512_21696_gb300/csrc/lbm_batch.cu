@@ -32,7 +32,7 @@ namespace lbm {
 // waiting), largest runs first; an item is (run, column, z-chunk).  Each run
 // is a self-contained lattice whose slots, cell types, gray records and
 // fields sit at its own offsets of the batch buffers.
-template <int TX, int TY, int MINB, bool MACRO, class LY>
+template <int TX, int TY, int MINB, bool MACRO, bool HELD, class LY>
 __global__ void __launch_bounds__(TX *TY, MINB)
     k_fused_batch(DevParams P, const BatchRun *__restrict__ runs, int nruns, int nitems,
                   unsigned int *__restrict__ counter, const unsigned char *__restrict__ fin,
@@ -60,13 +60,14 @@ __global__ void __launch_bounds__(TX *TY, MINB)
         G.n = R.n;
         for (int a = 0; a < 2; ++a)
             for (int d = 0; d < 3; ++d) G.accel[a][d] = R.accel[a][d];
+        for (int k = 0; k < 8; ++k) (&G.held[0][0][0])[k] = (&R.held[0][0][0])[k];
         const int local = item - R.item0;
         const int col = local % R.ncol, chunk = local / R.ncol;
         const int za = (int)((long long)R.nz * chunk / R.zchunks);
         const int zb = (int)((long long)R.nz * (chunk + 1) / R.zchunks);
         if (za >= zb) continue;
         const LY ly = LY::make(fin + R.pop_off, fout + R.pop_off, R.n);
-        fused_item<TX, TY, MACRO>(P, G, ly, type + R.cell_off, gray + R.cell_off, macro + 6 * R.cell_off,
+        fused_item<TX, TY, MACRO, HELD>(P, G, ly, type + R.cell_off, gray + R.cell_off, macro + 6 * R.cell_off,
                                   (col % R.tiles_x) * TX, (col / R.tiles_x) * TY, za, zb, smem_raw);
     }
 }
@@ -82,10 +83,10 @@ struct TileShape {
 constexpr TileShape BATCH_TILES[] = {{32, 8, 2}, {16, 16, 2}, {32, 16, 1}};
 constexpr int N_BATCH_TILES = 3;
 
-template <int TX, int TY, int MINB, bool MACRO, class LY>
+template <int TX, int TY, int MINB, bool MACRO, bool HELD, class LY>
 cudaError_t prep_kernel(int *slots, int dev)
 {
-    auto kern = lbm::k_fused_batch<TX, TY, MINB, MACRO, LY>;
+    auto kern = lbm::k_fused_batch<TX, TY, MINB, MACRO, HELD, LY>;
     const size_t smem = lbm::Tiles<TX, TY>::smem();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -127,6 +128,7 @@ struct lbm_batch {
     };
     std::vector<Group> groups;
     bool groups_ok = false;
+    bool held = false;  // some run has reservoir cells: launch the march that handles them
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (steps, parity)
     cudaStream_t cap = nullptr;  // private stream the graphs are captured on
 };
@@ -165,6 +167,7 @@ lbm::BatchRun describe_run(const lbm_batch *b, int r, const TileShape &ts, int p
     R.pop_off = b->pop_off[r];
     for (int a = 0; a < 2; ++a)
         for (int d = 0; d < 3; ++d) R.accel[a][d] = (float)p.body_accel[a][d];
+    for (int k = 0; k < 8; ++k) (&R.held[0][0][0])[k] = (&b->views[r]->dp.held[0][0][0])[k];
     return R;
 }
 
@@ -224,12 +227,12 @@ cudaError_t launch_group_t(lbm_batch *b, const lbm_batch::Group &g, bool macro)
     cudaError_t e = cudaMemsetAsync(g.counter, 0, sizeof(unsigned int), b->stream);
     if (e != cudaSuccess) return e;
     const lbm::DevParams &P = b->views[0]->dp;
-    if (macro)
-        lbm::k_fused_batch<TX, TY, MINB, true, LY><<<g.grid, TX * TY, smem, b->stream>>>(
-            P, g.d_runs, g.nruns, g.nitems, g.counter, fin, fout, b->type, b->gray, b->macro);
-    else
-        lbm::k_fused_batch<TX, TY, MINB, false, LY><<<g.grid, TX * TY, smem, b->stream>>>(
-            P, g.d_runs, g.nruns, g.nitems, g.counter, fin, fout, b->type, b->gray, b->macro);
+    auto kern = macro ? (b->held ? lbm::k_fused_batch<TX, TY, MINB, true, true, LY>
+                                 : lbm::k_fused_batch<TX, TY, MINB, true, false, LY>)
+                      : (b->held ? lbm::k_fused_batch<TX, TY, MINB, false, true, LY>
+                                 : lbm::k_fused_batch<TX, TY, MINB, false, false, LY>);
+    kern<<<g.grid, TX * TY, smem, b->stream>>>(P, g.d_runs, g.nruns, g.nitems, g.counter, fin, fout, b->type,
+                                               b->gray, b->macro);
     return cudaGetLastError();
 }
 
@@ -255,9 +258,11 @@ cudaError_t launch_group(lbm_batch *b, const lbm_batch::Group &g, bool macro)
 template <int TX, int TY, int MINB, class LY>
 cudaError_t prep_t(int *slots, int dev)
 {
-    cudaError_t e = prep_kernel<TX, TY, MINB, true, LY>(slots, dev);
+    cudaError_t e = prep_kernel<TX, TY, MINB, true, false, LY>(slots, dev);
+    if (e == cudaSuccess) e = prep_kernel<TX, TY, MINB, false, false, LY>(slots, dev);
+    if (e == cudaSuccess) e = prep_kernel<TX, TY, MINB, true, true, LY>(slots, dev);
     if (e != cudaSuccess) return e;
-    return prep_kernel<TX, TY, MINB, false, LY>(slots, dev);
+    return prep_kernel<TX, TY, MINB, false, true, LY>(slots, dev);
 }
 template <int TX, int TY, int MINB>
 cudaError_t prep_s(const lbm_batch *b, int *slots)
@@ -277,6 +282,18 @@ int slots_for(const lbm_batch *b, int tile, int *slots)
     default: e = prep_s<32, 8, 2>(b, slots); break;
     }
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "batch kernel setup");
+}
+
+// Picks the march for the runs' geometries (with or without reservoir
+// cells); a change drops the captured graphs.
+void sync_held(lbm_batch *b)
+{
+    bool held = false;
+    for (auto *v : b->views) held = held || v->n_held > 0;
+    if (held != b->held) {
+        b->held = held;
+        free_graphs(b);
+    }
 }
 
 // nsteps steps of the current groups, enqueued on the stream.
@@ -346,7 +363,9 @@ int lbm_batch_create(lbm_batch **out, int nruns, const lbm_params *runs)
         v->dev = b->dev;
         v->stream = b->stream;
         v->view = true;
+        v->owner = b;
         for (int k = 0; k < LBM_MAX_PORE_TYPES; ++k) lbm_default_constitutive(&v->curves[k]);
+        default_held(v);
         fill_device_params(v);
         b->views.push_back(v);
         b->cell_off.push_back(b->cells);
@@ -422,6 +441,7 @@ int lbm_batch_step(lbm_batch *b, int nsteps)
     if (nsteps == 0) return LBM_OK;
     DeviceGuard dg(b->dev);
     if (!dg.ok) return LBM_ERR_CUDA;
+    sync_held(b);
     if (!b->groups_ok) {
         std::vector<int> all(b->views.size());
         for (size_t r = 0; r < all.size(); ++r) all[r] = (int)r;
@@ -471,6 +491,7 @@ int lbm_batch_tune(lbm_batch *b, int trial_steps, int *tiles_out)
         if (!v->has_fields || v->cur != b->cur) return LBM_ERR_STATE;
     DeviceGuard dg(b->dev);
     if (!dg.ok) return LBM_ERR_CUDA;
+    sync_held(b);
     trial_steps += trial_steps & 1;  // even: the buffer parity returns
     // save the state the trials advance (populations, residual flags, fields)
     const size_t gray_bytes = (size_t)b->cells * sizeof(lbm::GrayRec), macro_bytes = 6 * (size_t)b->cells * 4;
@@ -595,3 +616,10 @@ int lbm_batch_observables(lbm_batch *b, lbm_obs *out)
 }
 
 }  // extern "C"
+
+// A view changed a per-run parameter (its reservoir densities): the item
+// tables, which carry them, are rebuilt before the next step.
+void lbm::batch_runs_changed(lbm_batch *b)
+{
+    if (b) b->groups_ok = false;
+}

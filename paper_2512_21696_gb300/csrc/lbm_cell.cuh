@@ -155,6 +155,34 @@ __device__ __forceinline__ CompMom finish_moments(const PullSums &p, int f0)
     return finish_moments_d(p, f0, density_dev(p.Id, p.d));
 }
 
+// ---- reservoir (pressure) cells ---------------------------------------------
+// An inlet / outlet cell holds its prescribed densities at rest: its moments
+// are the held density, no momentum and the second moment of the rest
+// equilibrium, so that the collision returns that equilibrium.
+__device__ __forceinline__ ff held_rho(const float (&held)[2][2][2], int t, int a)
+{
+    // a select, not an index, so that the parameter block stays out of local memory
+    return t == CELL_OUTLET ? ff{held[1][a][0], held[1][a][1]} : ff{held[0][a][0], held[0][a][1]};
+}
+// rho - 3 f_0 of a reservoir cell whose stored rest population is f0.
+__device__ __forceinline__ ff held_dev(ff rho, int f0) { return ff_add(rho, ff_from_ll(-3LL * f0, FIX_INV)); }
+// Moments relative to a reference rest population f_r with dff = rho - 3 f_r.
+__device__ __forceinline__ CompMom held_moments(ff rho, ff dff)
+{
+    CompMom m;
+    m.dr = dff.hi;
+    m.rho = rho;
+    const float d3 = dff.hi * (1.0f / 3.0f);  // sum c c (f^eq - 3 w f_r) = (rho - 3 f_r)/3 I
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        m.j[d] = {0.f, 0.f};
+        m.Ij[d] = 0;
+        m.S[d] = d3;
+        m.S[3 + d] = 0.f;
+    }
+    return m;
+}
+
 // Accumulates the FP32 parts of grad(rho^a) (e = rho^a(x+c_i) - rho^a(x)
 // without the rest-population part) and, in gray cells, grad(At) with the
 // neighbour densities nA, nB.
@@ -310,6 +338,7 @@ struct StoreLP {
 struct Geo {
     int nx, ny, nz, n;
     float accel[2][3];
+    float held[2][2][2];  // reservoir densities, as DevParams::held
 };
 __device__ __forceinline__ Geo geo_of(const DevParams &P)
 {
@@ -320,6 +349,7 @@ __device__ __forceinline__ Geo geo_of(const DevParams &P)
     G.n = P.n;
     for (int a = 0; a < 2; ++a)
         for (int d = 0; d < 3; ++d) G.accel[a][d] = P.accel[a][d];
+    for (int k = 0; k < 8; ++k) (&G.held[0][0][0])[k] = (&P.held[0][0][0])[k];
     return G;
 }
 
@@ -331,6 +361,7 @@ struct BatchRun {
     long long cell_off;  // first cell of the run in the per-cell arrays
     long long pop_off;   // byte offset of the run in each population buffer
     float accel[2][3];
+    float held[2][2][2];  // reservoir densities of the run
 };
 
 // ---- rest-referenced layouts ----------------------------------------------

@@ -66,6 +66,7 @@ struct DevParams {
     float s_lo, s_hi, at_cut, eps_n, kr_min;
     float at_wall;         // Atwood number of the wall densities
     float rho0[2];         // shift of the 16-bit storages: f_i - w_i rho0
+    float held[2][2][2];   // inlet [0] / outlet [1] densities (A, B) as float-float (hi, lo)
     int storage;           // enum lbm_storage
     Curve curve[MAX_TYPES];
 };
@@ -82,7 +83,15 @@ struct __align__(16) GrayRec {
 constexpr unsigned META_WET = 1u << 8;
 constexpr unsigned META_SWITCHED = 1u << 9;
 
-enum : uint8_t { CELL_PORE = LBM_CELL_PORE, CELL_SOLID = LBM_CELL_SOLID, CELL_GRAY = LBM_CELL_GRAY };
+enum : uint8_t {
+    CELL_PORE = LBM_CELL_PORE,
+    CELL_SOLID = LBM_CELL_SOLID,
+    CELL_GRAY = LBM_CELL_GRAY,
+    CELL_INLET = LBM_CELL_INLET,
+    CELL_OUTLET = LBM_CELL_OUTLET
+};
+// Reservoir (pressure) cell: held at the inlet or outlet densities.
+__host__ __device__ __forceinline__ bool is_held(int t) { return t == CELL_INLET || t == CELL_OUTLET; }
 
 // Neighbour coordinate along one axis: wrapped when periodic, -1 outside.
 __device__ __forceinline__ int axis_nb(int v, int d, int n, int periodic)

@@ -13,6 +13,9 @@
 
 struct lbm_ctx {
     lbm_params p;
+    double rho_held[2][2];       // densities (A, B) of the inlet [0] and outlet [1] cells
+    long long n_held = 0;        // number of inlet / outlet cells in the geometry
+    struct lbm_batch *owner = nullptr;  // the batch of a view
     int dev = 0;
     cudaStream_t stream = nullptr;
     int n = 0;
@@ -52,6 +55,9 @@ namespace lbm {
 // number of FP64 values it returns.
 int obs_blocks(int n);
 constexpr int NOBS_HOST = 16;
+
+// A run of the batch changed a per-run parameter: its next step re-reads the runs.
+void batch_runs_changed(struct lbm_batch *b);
 
 // Kernel launches (each records itself in ctx->launches and, while profiling,
 // brackets the launch with CUDA events).

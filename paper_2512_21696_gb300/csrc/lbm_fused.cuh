@@ -57,8 +57,10 @@ __device__ __forceinline__ int ring3(int p) { return ((p % 3) + 3) % 3; }
 
 // One work item: the TX x TY columns at (x0, y0) over planes [za, zb) of the
 // lattice of shape G (G.n is the slot stride of ly, type, gray and macro),
-// physics P.  Ends with a block barrier, so the rings can be reused at once.
-template <int TX, int TY, bool MACRO, class LY>
+// physics P.  HELD compiles in the reservoir (inlet / outlet) cells; without
+// it those cell types are not expected.  Ends with a block barrier, so the
+// rings can be reused at once.
+template <int TX, int TY, bool MACRO, bool HELD, class LY>
 __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, const LY &ly,
                                            const uint8_t *__restrict__ type,
                                            GrayRec *__restrict__ gray, float *__restrict__ macro, int x0, int y0,
@@ -110,6 +112,7 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
             if (me.type != CELL_SOLID) {
                 g = wrap_coord(x0 - 1 + dx, G.nx, P.per[0]) +
                     G.nx * (wrap_coord(y0 - 1 + dy, G.ny, P.per[1]) + G.ny * gz);
+                const bool held = HELD && is_held(me.type);
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
                     const int f0 = a ? me.f0B : me.f0A;
@@ -123,7 +126,8 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
                         acc += ly.mov_in(a, i, g);
                         if (src.type != CELL_SOLID) id += (long long)((a ? src.f0B : src.f0A) - f0) * w12(i);
                     }
-                    const ff v = density_dev(id, acc);
+                    ff v = density_dev(id, acc);
+                    if (held) v = held_dev(held_rho(G.held, me.type, a), f0);  // a reservoir's density is the held one
                     if (a) {
                         dc.drB = v.hi;
                         dc.loB = v.lo;
@@ -187,10 +191,15 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
             }
             M[a] = finish_moments_d(p, f0i[a], a ? ff{dc.drB, dc.loB} : ff{dc.drA, dc.loA});
         }
-        const float r[2] = {M[0].rho.hi, M[1].rho.hi};
         const uint8_t t = (uint8_t)me.type;
+        const bool held = HELD && is_held(t);
+        if (held) {  // reservoir: held density at rest, no force
+            M[0] = held_moments(held_rho(G.held, t, 0), ff{dc.drA, dc.loA});
+            M[1] = held_moments(held_rho(G.held, t, 1), ff{dc.drB, dc.loB});
+        }
+        const float r[2] = {M[0].rho.hi, M[1].rho.hi};
         const bool is_gray = (t == CELL_GRAY);
-        const bool csf = P.kappa != 0.0f && (P.csf_everywhere || is_gray);
+        const bool csf = !held && P.kappa != 0.0f && (P.csf_everywhere || is_gray);
         float gf[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, gAt[3] = {0.f, 0.f, 0.f};
         HessSum hA, hB;
         hess_zero(hA);
@@ -215,8 +224,16 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
             const DenMeta &tm = (cz(i) < 0 ? m0 : (cz(i) > 0 ? m2 : m1))[dk + cx(i) + T::DX * cy(i)];
             return (size_t)i * n + tm.gidx;
         };
+        float acc[2][3];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                acc[a][d] = held ? 0.f : G.accel[a][d];
+                if (held) gf[a][d] = 0.f;
+            }
         StoreRest<LY> st{ly, c, {f0i[0], f0i[1]}};
-        collide_store<MACRO>(P, G.accel, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
+        collide_store<MACRO>(P, acc, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
     };
 
     load_raw(za - 2);

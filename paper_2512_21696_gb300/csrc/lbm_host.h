@@ -12,8 +12,10 @@ namespace lbm_host {
 int cuda_fail(cudaError_t e, const char *where);
 // LBM_OK or LBM_ERR_ARG for a parameter block (the checks of lbm_create).
 int validate_params(const lbm_params *p);
-// Fills ctx->dp from ctx->p and the constitutive curves.
+// Fills ctx->dp from ctx->p, the reservoir densities and the constitutive curves.
 void fill_device_params(lbm_ctx *ctx);
+// Reservoir densities before any lbm_set_pressure: (rho_hi, rho_lo) at both ends.
+void default_held(lbm_ctx *ctx);
 // Bytes of one population buffer of ctx (2 components, its storage).
 size_t pop_bytes(const lbm_ctx *ctx);
 

@@ -76,8 +76,13 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                     dc.type = type[gi];
                     if (dc.type != CELL_SOLID) {
                         g = gi;
-                        dc.rA = density_lp<H>(fin + g, n, P.rho0[0]);
-                        dc.rB = density_lp<H>(fin + (size_t)Q * n + g, n, P.rho0[1]);
+                        if (is_held(dc.type)) {  // reservoir: the held densities
+                            dc.rA = held_rho(P.held, dc.type, 0).hi;
+                            dc.rB = held_rho(P.held, dc.type, 1).hi;
+                        } else {
+                            dc.rA = density_lp<H>(fin + g, n, P.rho0[0]);
+                            dc.rB = density_lp<H>(fin + (size_t)Q * n + g, n, P.rho0[1]);
+                        }
                         dc.at = atwood_rho(P.wet, dc.rA, dc.rB);
                     }
                 }
@@ -113,12 +118,18 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                 if (nd.type == CELL_SOLID) wall |= 1u << i;
             }
             CompMom M[2];
-            M[0] = moments_lp<H>(fin + c, n, P.rho0[0]);
-            M[1] = moments_lp<H>(fin + (size_t)Q * n + c, n, P.rho0[1]);
-            const float r[2] = {M[0].rho.hi, M[1].rho.hi};
             const uint8_t t = (uint8_t)me.type;
+            const bool held = is_held(t);
+            if (held) {  // reservoir: held density at rest (reference rho/3), no force
+                M[0] = held_moments(ff{me.rA, 0.f}, ff{0.f, 0.f});
+                M[1] = held_moments(ff{me.rB, 0.f}, ff{0.f, 0.f});
+            } else {
+                M[0] = moments_lp<H>(fin + c, n, P.rho0[0]);
+                M[1] = moments_lp<H>(fin + (size_t)Q * n + c, n, P.rho0[1]);
+            }
+            const float r[2] = {M[0].rho.hi, M[1].rho.hi};
             const bool is_gray = (t == CELL_GRAY);
-            const bool csf = P.kappa != 0.0f && (P.csf_everywhere || is_gray);
+            const bool csf = !held && P.kappa != 0.0f && (P.csf_everywhere || is_gray);
             float gf[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, gAt[3] = {0.f, 0.f, 0.f};
             HessSum hA, hB;
             hess_zero(hA);
@@ -140,8 +151,16 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                 if (wall & (1u << i)) return (size_t)opp(i) * n + c;
                 return (size_t)i * n + (cz(i) < 0 ? g0 : (cz(i) > 0 ? g2 : g1))[dk + cx(i) + T::DX * cy(i)];
             };
+            float acc[2][3];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    acc[a][d] = held ? 0.f : P.accel[a][d];
+                    if (held) gf[a][d] = 0.f;
+                }
             StoreLP<H> st{fout, n, c, {r[0] * (1.0f / 3.0f), r[1] * (1.0f / 3.0f)}, {P.rho0[0], P.rho0[1]}, {0.f, 0.f}};
-            collide_store<MACRO>(P, P.accel, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
+            collide_store<MACRO>(P, acc, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
         };
 
         densities(za - 1);

@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs 
         const int x = c % P.nx, y = (c / P.nx) % P.ny, z = c / (P.nx * P.ny);
         acc[0] += (double)ra;
         acc[1] += (double)rb;
-        const float phc = t == CELL_GRAY ? phi[c] : 1.0f;
+        // saturation weight: phi in gray cells, 1 in pores, reservoirs left out
+        const float phc = t == CELL_GRAY ? phi[c] : (t == CELL_PORE ? 1.0f : 0.0f);
         acc[2] += (double)(phc * sw);
         acc[3] += (double)phc;
         if (x == P.nx - 1) acc[4] += (double)u0;

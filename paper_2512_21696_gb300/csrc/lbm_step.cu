@@ -184,7 +184,17 @@ __global__ void __launch_bounds__(256) k_density(DevParams P, const float *__res
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = P.n;
     if (c >= n) return;
-    if (type[c] == CELL_SOLID) return;
+    const uint8_t t = type[c];
+    if (t == CELL_SOLID) return;
+    if (is_held(t)) {  // reservoir: the held densities
+        for (int a = 0; a < 2; ++a)
+            drho[(size_t)a * n + c] =
+                held_dev(held_rho(P.held, t, a), reinterpret_cast<const int *>(f + (size_t)a * Q * n)[c]).hi;
+        drho[(size_t)2 * n + c] = atwood_of(P.wet, reinterpret_cast<const int *>(f)[c],
+                                            reinterpret_cast<const int *>(f + (size_t)Q * n)[c], drho[c],
+                                            drho[n + c]);
+        return;
+    }
     int x, y, z;
     cell_xyz(c, P, x, y, z);
     const Axes A = axes_of(P, x, y, z);
@@ -265,14 +275,19 @@ __global__ void __launch_bounds__(256) k_collide(DevParams P, const float *__res
         }
         f0i[a] = f0;
         M[a] = finish_moments(p, f0);
+        if (is_held(t)) {  // reservoir: held density at rest, no force
+            const ff rh = held_rho(P.held, t, a);
+            M[a] = held_moments(rh, held_dev(rh, f0));
+        }
     }
+    const bool held = is_held(t);
     const float r[2] = {M[0].rho.hi, M[1].rho.hi};
     const bool is_gray = (t == CELL_GRAY);
 
     // ---- density stencils: FP32 parts of grad(rho^a) (drho differences; walls
     //      contribute rho_wall - rho(x)), grad(At) in gray cells, and the
     //      Hessians of rho^A, rho^B where Eq. 4 applies ------------------------
-    const bool csf = P.kappa != 0.0f && (P.csf_everywhere || is_gray);
+    const bool csf = !held && P.kappa != 0.0f && (P.csf_everywhere || is_gray);
     float gf[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, gAt[3] = {0.f, 0.f, 0.f};
     HessSum hA, hB;
     hess_zero(hA);
@@ -296,8 +311,16 @@ __global__ void __launch_bounds__(256) k_collide(DevParams P, const float *__res
     auto tgt = [&](int i) -> size_t {
         return (wall & (1u << i)) ? (size_t)opp(i) * n + c : (size_t)i * n + nb[i];
     };
+    float acc[2][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            acc[a][d] = held ? 0.f : P.accel[a][d];
+            if (held) gf[a][d] = 0.f;
+        }
     StoreRest<LayF32> st{LayF32{fin, fout, n}, c, {f0i[0], f0i[1]}};
-    collide_store<MACRO>(P, P.accel, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
+    collide_store<MACRO>(P, acc, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
 }
 
 // ---------------------------------------------------------------------------

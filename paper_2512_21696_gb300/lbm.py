@@ -12,7 +12,8 @@ import ctypes as C
 import numpy as np
 
 from . import _lib as L
-from ._lib import (LBM_CELL_GRAY, LBM_CELL_PORE, LBM_CELL_SOLID, LBM_MEM_DEVICE, LBM_MEM_HOST,
+from ._lib import (LBM_CELL_GRAY, LBM_CELL_INLET, LBM_CELL_OUTLET, LBM_CELL_PORE, LBM_CELL_SOLID,
+                   LBM_MEM_DEVICE, LBM_MEM_HOST,
                    LBM_STORAGE_BF16S, LBM_STORAGE_F16S, LBM_STORAGE_F32, lbm_constitutive,
                    lbm_params)
 
@@ -21,6 +22,7 @@ __all__ = [
     "lbm_destroy", "lbm_set_constitutive", "lbm_set_geometry", "lbm_init_fields", "lbm_step",
     "lbm_observables", "lbm_get_fields", "lbm_get_static", "lbm_save_state", "lbm_load_state",
     "lbm_profile", "lbm_profile_read", "lbm_launch_count", "lbm_abi_version", "lbm_observables_noalloc", "lbm_set_kernel",
+    "lbm_set_pressure", "LBM_CELL_INLET", "LBM_CELL_OUTLET",
     "LBM_CELL_PORE", "LBM_CELL_SOLID", "LBM_CELL_GRAY", "LBM_STORAGE_F32", "LBM_STORAGE_F16S",
     "LBM_STORAGE_BF16S",
 ]
@@ -176,6 +178,13 @@ def lbm_init_fields(ctx: LbmContext, rhoA, rhoB, u=None) -> None:
 
 def lbm_step(ctx: LbmContext, nsteps: int = 1) -> None:
     _check(L.load().lbm_step(ctx.handle, int(nsteps)), "lbm_step")
+
+
+def lbm_set_pressure(ctx: LbmContext, rho_in, rho_out) -> None:
+    """Densities (A, B) held in the inlet and in the outlet cells from the next step."""
+    a = (C.c_double * 2)(*[float(v) for v in rho_in])
+    b = (C.c_double * 2)(*[float(v) for v in rho_out])
+    _check(L.load().lbm_set_pressure(ctx.handle, a, b), "lbm_set_pressure")
 
 
 def lbm_observables(ctx: LbmContext, check: bool = True) -> dict:

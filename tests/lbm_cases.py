@@ -14,7 +14,7 @@ from paper_2512_21696_gb300 import synth
 DEFAULTS = dict(G=0.0, kappa=0.0, tau=(1.0, 1.0), accel=((0, 0, 0), (0, 0, 0)), csf_everywhere=0,
                 rho_wall=(0.515, 0.515), wet=1, rho_hi=1.0, rho_lo=0.03, periodic=(1, 1, 1),
                 s_lo=0.1, s_hi=0.9, at_cut=0.95, kr_min=1e-6, c_g=1.0, phi_avg=(0.515, 0.515),
-                phi_max=(1.0, 1.0))
+                phi_max=(1.0, 1.0), held=None)
 CURVE = dict(kc_d=1.0, pd=0.02, lam=2.0, swr=0.15, nw=3.0, nn=2.0, phi_ref=0.35, f_max=3.5,
              f_min=0.575, aniso=1.0)
 
@@ -95,6 +95,8 @@ def run_gpu(case: Case, steps: int, device_arrays=False, path=0, tile=0, **extra
         else:
             lbm.lbm_set_geometry(ctx, case.cell, case.phi32, case.ptype)
             lbm.lbm_init_fields(ctx, case.rhoA32, case.rhoB32, case.u32)
+        if case.s["held"] is not None:
+            lbm.lbm_set_pressure(ctx, *case.s["held"])
         lbm.lbm_step(ctx, steps)
         fields = lbm.lbm_get_fields(ctx)
         obs = lbm.lbm_observables(ctx, check=False)
@@ -111,6 +113,8 @@ def make_oracle(case: Case):
                  curves=curves)
     o.init_fields(case.rhoA32.astype(np.float64), case.rhoB32.astype(np.float64),
                   None if case.u32 is None else case.u32.astype(np.float64))
+    if case.s["held"] is not None:
+        o.set_pressure(*case.s["held"])
     return o
 
 
@@ -173,6 +177,25 @@ def fiber_flow(n=24, axis=0, seed=synth.SEED_BASE + 2, ncyl=12, aniso=10.0, g=1e
     return Case(f"fiber{n}_{'xyz'[axis]}", shape, cell, phi, np.full(shape, 0.03), np.full(shape, 1.0),
                 ptype=ptype, curves=[dict(CURVE, aniso=aniso)], G=1.1, accel=((0, 0, 0), tuple(acc)),
                 rho_wall=(0.03, 1.0), wet=1)
+
+
+def imbibition(n=32, seed=synth.SEED_BASE + 6, dp=0.02, tau=(1.0, 1.0), nz=None):
+    """Pressure-driven imbibition (the set-ups of Sec. I and the Appendix):
+    the synthetic multiscale rock between an inlet reservoir plane of wetting
+    B (z = 0, rho_B = 1 + dp) and an outlet plane of non-wetting A
+    (z = nz - 1), z not periodic.  The rock starts filled with A except a B
+    slab next to the inlet.  Held densities are FP32-representable."""
+    cell, phi, ptype = synth.drainage_geometry(n, seed)
+    nz = nz or n
+    cell, phi, ptype = cell[:nz].copy(), phi[:nz], ptype[:nz]
+    cell[0], cell[-1] = synth.INLET, synth.OUTLET
+    zz = np.arange(nz)[:, None, None] + np.zeros(cell.shape, np.int64)
+    wet = zz < 4
+    rA, rB = np.where(wet, 0.03, 1.0), np.where(wet, 1.0, 0.03)
+    f32 = lambda v: float(np.float32(v))
+    held = ((f32(0.03), f32(1.0 + dp)), (f32(1.0), f32(0.03)))
+    return Case(f"imbibition{cell.shape}", cell.shape, cell, phi, rA, rB, ptype=ptype, G=1.1, kappa=-0.045,
+                tau=tau, rho_wall=(0.03, 1.0), wet=1, periodic=(1, 1, 0), held=held)
 
 
 def adjoint_case(n=8, seed=21, shape=None, steps_hint=None):

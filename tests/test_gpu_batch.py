@@ -63,9 +63,10 @@ def test_batch_runs_match_single_lattices_and_oracle(storage):
     for case, g in zip(cases, got):
         alone, _, _ = LC.run_gpu(case, 12, storage=storage, tile=2)
         # the batched and single-lattice kernels are separate compilations of
-        # the same march; a last-bit FP32 difference can flip one 16-bit
-        # rounding of a stored deviation (~1e-6 of the fields under F16R)
-        _close(g, alone, 1e-6 if storage == 0 else 1e-5)
+        # the same march; a last-bit FP32 difference can flip a 16-bit
+        # rounding of a stored deviation (~1e-6 of the fields under F16R),
+        # which the following steps carry to a few 1e-5 at that cell
+        _close(g, alone, 1e-6 if storage == 0 else 5e-5)
         if storage == 0:
             of, _, _ = LC.run_oracle(case, 12)
             fl = case.cell != synth.SOLID

@@ -1,0 +1,173 @@
+"""Pressure (reservoir) boundaries of the CUDA step against the FP64 oracle.
+
+Inlet / outlet cells hold prescribed component densities at rest (the
+reading of the imbibition set-ups of Sec. I and the Appendix).  Parity as in
+the other GPU tests: relative 1e-5 in the L2 norm over non-solid cells for
+rho^A, rho^B, u and Sw, FP32 kernels against the FP64 oracle on identical
+FP32 inputs; the 16-bit storages are bounded like their other accuracy
+tests.
+"""
+import numpy as np
+import pytest
+
+import lbm_cases as LC
+from helpers import rel_l2
+from paper_2512_21696_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+KERNELS = [(0, 0), (0, 1), (0, 2), (0, 3), (0, 4), (1, 0)]  # (path, tile): fused tiles 0-4, two launches
+
+
+def _errs(case, gpu, orc):
+    (ga, gb, gu, gs), (oa, ob, ou, osw) = gpu, orc
+    fl = case.cell != synth.SOLID
+    return dict(rhoA=rel_l2(ga, oa, fl), rhoB=rel_l2(gb, ob, fl), u=rel_l2(gu, ou, fl), sw=rel_l2(gs, osw, fl))
+
+
+def _assert_parity(case, gpu, orc, tol=TOL):
+    e = _errs(case, gpu, orc)
+    assert max(e.values()) <= tol, f"{case.name}: {e}"
+    return e
+
+
+def _setup(ctx, case):
+    from paper_2512_21696_gb300 import lbm
+    for k, cv in enumerate(case.curves):
+        lbm.lbm_set_constitutive(ctx, k, lbm.lbm_default_constitutive(
+            kc_d=cv["kc_d"], pd=cv["pd"], lam=cv["lam"], swr=cv["swr"], nw=cv["nw"], nn=cv["nn"],
+            phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"]))
+    lbm.lbm_set_geometry(ctx, case.cell, case.phi32, case.ptype)
+    lbm.lbm_init_fields(ctx, case.rhoA32, case.rhoB32, case.u32)
+    lbm.lbm_set_pressure(ctx, *case.s["held"])
+
+
+@pytest.mark.parametrize("path,tile", KERNELS)
+def test_imbibition_every_kernel(path, tile):
+    case = LC.imbibition(16)
+    gf, _, _ = LC.run_gpu(case, 40, path=path, tile=tile)
+    of, _, _ = LC.run_oracle(case, 40)
+    _assert_parity(case, gf, of)
+
+
+def test_imbibition_400_steps():
+    """32^3 multiscale rock between a wetting inlet and a non-wetting outlet
+    reservoir, 400 FP32 steps: fields and observables against the oracle."""
+    case = LC.imbibition(32)
+    gf, gobs, _ = LC.run_gpu(case, 400)
+    of, oobs, _ = LC.run_oracle(case, 400)
+    e = _assert_parity(case, gf, of)
+    assert gobs["nan_count"] == 0
+    assert abs(gobs["sat"] - oobs["sat"]) < 1e-6
+    assert abs(gobs["flux_vol"][2] - oobs["flux_vol"][2]) < 1e-5 * abs(oobs["flux_vol"][2])
+    print("imbibition errors", e, "sat", gobs["sat"], oobs["sat"])
+
+
+def test_imbibition_regularised_tau_ragged():
+    case = LC.imbibition(24, tau=(0.7, 0.9), nz=19)
+    gf, _, _ = LC.run_gpu(case, 150)
+    of, _, _ = LC.run_oracle(case, 150)
+    _assert_parity(case, gf, of)
+
+
+def test_reservoir_cells_hold_their_densities():
+    case = LC.imbibition(16)
+    (ra, rb, u, sw), _, _ = LC.run_gpu(case, 7)
+    (a_in, b_in), (a_out, b_out) = case.s["held"]
+    for plane, (a, b) in ((0, (a_in, b_in)), (-1, (a_out, b_out))):
+        assert np.all(ra[plane] == np.float32(a)) and np.all(rb[plane] == np.float32(b))
+        assert np.all(u[:, plane] == 0.0)
+
+
+def test_pressure_ramp_matches_oracle():
+    """The held densities change between steps (the stepped pressure
+    difference of the imbibition protocol)."""
+    from paper_2512_21696_gb300 import lbm
+    case = LC.imbibition(16)
+    levels = [((0.03, 1.04), (1.0, 0.03)), ((0.03, 1.0), (1.01, 0.03)), ((0.04, 1.02), (0.98, 0.05))]
+    levels = [tuple(tuple(float(np.float32(v)) for v in side) for side in lv) for lv in levels]
+    ctx = lbm.lbm_create(LC.gpu_params(case))
+    o = LC.make_oracle(case)
+    try:
+        _setup(ctx, case)
+        for lv in levels:
+            lbm.lbm_set_pressure(ctx, *lv)
+            o.set_pressure(*lv)
+            lbm.lbm_step(ctx, 30)
+            o.step(30)
+        gf = lbm.lbm_get_fields(ctx)
+    finally:
+        ctx.close()
+    _assert_parity(case, gf, o.fields())
+
+
+# about 3x the saturation errors measured on a GB300 after 200 steps
+# (3.1e-4, 5.3e-3, 9.6e-7, 7.3e-6 for F16S, BF16S, F16R, BF16R)
+BOUND_SAT = {1: 1e-3, 2: 1.6e-2, 3: 3e-6, 4: 2.5e-5}
+
+
+@pytest.mark.parametrize("storage", [1, 2, 3, 4])
+def test_imbibition_16bit_storages(storage):
+    case = LC.imbibition(16)
+    _, gobs, _ = LC.run_gpu(case, 200, storage=storage)
+    _, oobs, _ = LC.run_oracle(case, 200)
+    err = abs(gobs["sat"] - oobs["sat"])
+    print(f"imbibition saturation, storage {storage}: gpu {gobs['sat']:.7f} oracle {oobs['sat']:.7f} err {err:.2e}")
+    assert gobs["nan_count"] == 0 and err <= BOUND_SAT[storage]
+
+
+def test_batch_runs_with_reservoirs_match_single_lattices():
+    """Runs of uneven size in one batch, each with its own held densities,
+    changed for one run between steps: the same as the lattices alone and
+    as the oracle."""
+    from paper_2512_21696_gb300 import lbm
+    cases = [LC.imbibition(16), LC.imbibition(24, nz=13, seed=synth.SEED_BASE + 7),
+             LC.imbibition(20, dp=0.05, seed=synth.SEED_BASE + 8)]
+    change = ((0.05, 1.0), (1.02, 0.03))
+    b = lbm.lbm_batch_create([LC.gpu_params(c) for c in cases])
+    try:
+        views = [lbm.lbm_batch_run(b, r) for r in range(len(cases))]
+        for v, c in zip(views, cases):
+            _setup(v, c)
+        lbm.lbm_batch_step(b, 20)
+        lbm.lbm_set_pressure(views[1], *change)
+        lbm.lbm_batch_step(b, 20)
+        got = [lbm.lbm_get_fields(v) for v in views]
+    finally:
+        b.close()
+    for r, (c, g) in enumerate(zip(cases, got)):
+        o = LC.make_oracle(c)
+        o.step(20)
+        if r == 1:
+            o.set_pressure(*change)
+        o.step(20)
+        _assert_parity(c, g, o.fields())
+        ctx = lbm.lbm_create(LC.gpu_params(c))
+        try:
+            _setup(ctx, c)
+            lbm.lbm_step(ctx, 20)
+            if r == 1:
+                lbm.lbm_set_pressure(ctx, *change)
+            lbm.lbm_step(ctx, 20)
+            alone = lbm.lbm_get_fields(ctx)
+        finally:
+            ctx.close()
+        for x, y in zip(g, alone):
+            np.testing.assert_allclose(x, y, rtol=0, atol=1e-6 * max(1.0, float(np.abs(y).max())))
+
+
+def test_invalid_pressure_and_adjoint_are_rejected():
+    from paper_2512_21696_gb300 import lbm
+    case = LC.imbibition(8)
+    ctx = lbm.lbm_create(LC.gpu_params(case))
+    try:
+        _setup(ctx, case)
+        for bad in (((-0.1, 1.0), (1.0, 0.03)), ((0.0, 0.0), (1.0, 0.03)), ((float("nan"), 1.0), (1.0, 0.03))):
+            with pytest.raises(lbm.LbmError) as ei:
+                lbm.lbm_set_pressure(ctx, *bad)
+            assert ei.value.code == -1
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_adjoint_run(ctx, 1e-3, 0.5, 4, 2)
+        assert ei.value.code == -1
+    finally:
+        ctx.close()
