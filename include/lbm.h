@@ -239,6 +239,24 @@ LBM_API int lbm_step(lbm_ctx *ctx, int nsteps);
  * LBM_ERR_ARG on a NULL pointer or invalid densities.  No device work. */
 LBM_API int lbm_set_pressure(lbm_ctx *ctx, const double rho_in[2], const double rho_out[2]);
 
+/* Stepped-pressure protocol of the imbibition set-ups (Sec. I: the pressure
+ * difference between the two boundaries is lowered level by level and a
+ * steady state is recorded at each level; the Appendix evaluates Pc(Sw) the
+ * same way).  For level k = 0 .. nlevels-1: hold rho_in[2k..2k+1] and
+ * rho_out[2k..2k+1] (as lbm_set_pressure), then step check_every steps at a
+ * time until the saturation (lbm_obs.sat, which leaves the reservoirs out)
+ * changed by at most sat_tol over the last check, or max_steps steps ran.
+ * sat[k] receives the saturation at the end of the level and steps[k] the
+ * steps it took.  The capillary pressure of a level is the reservoirs'
+ * pressure difference, p = (rhoA + rhoB)/3 + G rhoA rhoB at each end.
+ *   nlevels >= 1, check_every >= 1, sat_tol >= 0, max_steps >= 1; host arrays.
+ * Returns LBM_OK when every level became steady, LBM_ERR_TIMEOUT when some
+ * level ran out of steps (outputs still filled), LBM_ERR_STATE without
+ * reservoir cells or fields, LBM_ERR_ARG on invalid arguments (checked
+ * before the first step).  Synchronous. */
+LBM_API int lbm_pressure_levels(lbm_ctx *ctx, int nlevels, const double *rho_in, const double *rho_out,
+                                int check_every, double sat_tol, int max_steps, double *sat, int *steps);
+
 /* FP64 reductions of the current fields into *out (synchronises).
  * Returns LBM_ERR_NUMERIC when nan_count > 0 (out is still filled). */
 LBM_API int lbm_observables(lbm_ctx *ctx, lbm_obs *out);

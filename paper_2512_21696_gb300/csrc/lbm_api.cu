@@ -1,5 +1,6 @@
 // C-ABI entry points (include/lbm.h): validation, buffer ownership, stream
 // handling and the launch sequence of a time step.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -379,6 +380,42 @@ int lbm_set_pressure(lbm_ctx *ctx, const double rho_in[2], const double rho_out[
     fill_device_params(ctx);
     if (ctx->owner) lbm::batch_runs_changed(ctx->owner);
     return LBM_OK;
+}
+
+int lbm_pressure_levels(lbm_ctx *ctx, int nlevels, const double *rho_in, const double *rho_out, int check_every,
+                        double sat_tol, int max_steps, double *sat, int *steps)
+{
+    if (!ctx || nlevels < 1 || !rho_in || !rho_out || check_every < 1 || !(sat_tol >= 0.0) || max_steps < 1 ||
+        !sat || !steps)
+        return LBM_ERR_ARG;
+    for (int k = 0; k < 2 * nlevels; k += 2)
+        for (const double *r : {rho_in + k, rho_out + k})
+            if (!std::isfinite(r[0]) || !std::isfinite(r[1]) || r[0] < 0.0 || r[1] < 0.0 || !(r[0] + r[1] > 0.0))
+                return LBM_ERR_ARG;
+    if (!ctx->has_fields || ctx->n_held == 0) return LBM_ERR_STATE;
+    bool all = true;
+    for (int k = 0; k < nlevels; ++k) {
+        int rc = lbm_set_pressure(ctx, rho_in + 2 * k, rho_out + 2 * k);
+        lbm_obs o;
+        if (rc == LBM_OK) rc = lbm_observables(ctx, &o);
+        if (rc != LBM_OK) return rc;
+        double prev = o.sat;
+        int done = 0;
+        bool steady = false;
+        while (done < max_steps && !steady) {
+            const int m = std::min(check_every, max_steps - done);
+            rc = lbm_step(ctx, m);
+            if (rc == LBM_OK) rc = lbm_observables(ctx, &o);
+            if (rc != LBM_OK) return rc;
+            done += m;
+            steady = std::fabs(o.sat - prev) <= sat_tol;
+            prev = o.sat;
+        }
+        sat[k] = o.sat;
+        steps[k] = done;
+        all = all && steady;
+    }
+    return all ? LBM_OK : LBM_ERR_TIMEOUT;
 }
 
 int lbm_init_fields(lbm_ctx *ctx, const float *rhoA, const float *rhoB, const float *u, int mem)

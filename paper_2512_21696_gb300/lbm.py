@@ -22,7 +22,7 @@ __all__ = [
     "lbm_destroy", "lbm_set_constitutive", "lbm_set_geometry", "lbm_init_fields", "lbm_step",
     "lbm_observables", "lbm_get_fields", "lbm_get_static", "lbm_save_state", "lbm_load_state",
     "lbm_profile", "lbm_profile_read", "lbm_launch_count", "lbm_abi_version", "lbm_observables_noalloc", "lbm_set_kernel",
-    "lbm_set_pressure", "LBM_CELL_INLET", "LBM_CELL_OUTLET",
+    "lbm_set_pressure", "lbm_pressure_levels", "LBM_CELL_INLET", "LBM_CELL_OUTLET",
     "LBM_CELL_PORE", "LBM_CELL_SOLID", "LBM_CELL_GRAY", "LBM_STORAGE_F32", "LBM_STORAGE_F16S",
     "LBM_STORAGE_BF16S",
 ]
@@ -185,6 +185,20 @@ def lbm_set_pressure(ctx: LbmContext, rho_in, rho_out) -> None:
     a = (C.c_double * 2)(*[float(v) for v in rho_in])
     b = (C.c_double * 2)(*[float(v) for v in rho_out])
     _check(L.load().lbm_set_pressure(ctx.handle, a, b), "lbm_set_pressure")
+
+
+def lbm_pressure_levels(ctx: LbmContext, levels, check_every: int, sat_tol: float, max_steps: int):
+    """Stepped-pressure protocol: levels = [((rhoA_in, rhoB_in), (rhoA_out, rhoB_out)), ...].
+    Returns (all_steady, saturation per level, steps per level)."""
+    k = len(levels)
+    rin = (C.c_double * (2 * k))(*[float(v) for lv in levels for v in lv[0]])
+    rout = (C.c_double * (2 * k))(*[float(v) for lv in levels for v in lv[1]])
+    sat, steps = (C.c_double * k)(), (C.c_int * k)()
+    code = L.load().lbm_pressure_levels(ctx.handle, k, rin, rout, int(check_every), float(sat_tol),
+                                        int(max_steps), sat, steps)
+    if code not in (L.LBM_OK, L.LBM_ERR_TIMEOUT):
+        _check(code, "lbm_pressure_levels")
+    return code == L.LBM_OK, list(sat), list(steps)
 
 
 def lbm_observables(ctx: LbmContext, check: bool = True) -> dict:

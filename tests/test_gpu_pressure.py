@@ -171,3 +171,43 @@ def test_invalid_pressure_and_adjoint_are_rejected():
         assert ei.value.code == -1
     finally:
         ctx.close()
+
+
+def test_pressure_levels_protocol_matches_oracle():
+    """The stepped-pressure protocol: at each level the saturation it reports
+    after the steps it reports is the oracle's after the same steps, and a
+    higher wetting-reservoir pressure draws more wetting fluid in."""
+    from paper_2512_21696_gb300 import lbm
+    case = LC.imbibition(16)
+    f32 = lambda v: float(np.float32(v))
+    levels = [((f32(0.03), f32(rw)), (f32(1.0), f32(0.03))) for rw in (0.97, 1.0, 1.04)]
+    ctx = lbm.lbm_create(LC.gpu_params(case))
+    try:
+        _setup(ctx, case)
+        ok, sat, steps = lbm.lbm_pressure_levels(ctx, levels, 100, 2e-4, 2000)
+        obs = lbm.lbm_observables(ctx)
+    finally:
+        ctx.close()
+    print("levels", levels, "steady", ok, "sat", sat, "steps", steps)
+    assert all(0 < s <= 2000 and (s % 100 == 0 or s == 2000) for s in steps)
+    assert obs["sat"] == sat[-1] and obs["step"] == sum(steps)
+    o = LC.make_oracle(case)
+    for lv, n, s in zip(levels, steps, sat):
+        o.set_pressure(*lv)
+        o.step(n)
+        assert abs(o.observables()["sat"] - s) < 1e-5
+    assert sat[2] > sat[0]
+
+
+def test_pressure_levels_needs_reservoirs():
+    from paper_2512_21696_gb300 import lbm
+    case = LC.droplet(n=8, R=2)
+    ctx = lbm.lbm_create(LC.gpu_params(case))
+    try:
+        lbm.lbm_set_geometry(ctx, case.cell, case.phi32)
+        lbm.lbm_init_fields(ctx, case.rhoA32, case.rhoB32)
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_pressure_levels(ctx, [((0.03, 1.0), (1.0, 0.03))], 10, 1e-4, 100)
+        assert ei.value.code == -6
+    finally:
+        ctx.close()
