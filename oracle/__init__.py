@@ -49,7 +49,7 @@ class OrcParams(C.Structure):
 
 class OrcCurve(C.Structure):
     _fields_ = [(k, C.c_double) for k in
-                ("kc_d", "pd", "lambda_", "swr", "nw", "nn", "phi_ref", "f_max", "f_min", "aniso")]
+                ("kc_d", "pd", "lambda_", "swr", "nw", "nn", "phi_ref", "f_max", "f_min", "aniso", "thomeer_g")]
 
 
 def build(force: bool = False) -> str:
@@ -159,7 +159,7 @@ def make_params(shape, **kw) -> OrcParams:
 def make_curve(**kw) -> OrcCurve:
     c = OrcCurve()
     vals = dict(kc_d=1.0, pd=0.02, lambda_=2.0, swr=0.15, nw=3.0, nn=2.0, phi_ref=0.35,
-                f_max=3.5, f_min=0.575, aniso=1.0)
+                f_max=3.5, f_min=0.575, aniso=1.0, thomeer_g=0.0)
     if "lam" in kw:
         kw["lambda_"] = kw.pop("lam")
     vals.update(kw)

@@ -151,7 +151,13 @@ def geometry(cell, phi_gray, curve, c_g):
     lamL = torch.sqrt((kref / curve["phi_ref"]) / (K0 / phis))
 
     def sw_at(f):
-        se = torch.clamp((f / lamL) ** (-curve["lam"]), max=1.0)
+        x = f / lamL
+        if curve.get("thomeer_g", 0.0) > 0.0:
+            # Thomeer: log10(x) ln(1 - Se) = -G above entry (x > 1), Se = 1 below
+            xs = torch.where(x > 1.0, x, torch.full_like(x, 2.0))
+            se = torch.where(x > 1.0, -torch.expm1(-curve["thomeer_g"] / torch.log10(xs)), torch.ones_like(x))
+        else:
+            se = torch.clamp(x ** (-curve["lam"]), max=1.0)
         return curve["swr"] + (1 - curve["swr"]) * se
 
     z = lambda v: torch.where(gray, v, torch.zeros_like(v))
@@ -267,7 +273,14 @@ class Model:
         mag = torch.sqrt((dAt ** 2).sum(0))
         Hc = torch.where(torch.abs(At) <= p["at_cut"], 0.5 * mag, torch.zeros_like(mag))
         se_c = torch.clamp((sw - cv["swr"]) / (1 - cv["swr"]), 1e-2, 1.0)
-        Pc = geo["pcs"] * se_c ** (-1.0 / cv["lam"])
+        if cv.get("thomeer_g", 0.0) > 0.0:
+            # Thomeer: Pc = Pe 10^min(-G / ln(1 - Se), 1)
+            open_ = se_c < 1.0
+            ss = torch.where(open_, se_c, torch.full_like(se_c, 0.5))
+            ex = torch.where(open_, cv["thomeer_g"] / -torch.log1p(-ss), torch.zeros_like(se_c))
+            Pc = geo["pcs"] * torch.pow(10.0, torch.clamp(ex, max=1.0))
+        else:
+            Pc = geo["pcs"] * se_c ** (-1.0 / cv["lam"])
         nvec = dAt / torch.clamp(mag, min=p["eps_n"])
         for a in range(2):
             cap = -Pc[None] * (rho[a] / rt)[None] * nvec * Hc[None]

@@ -34,8 +34,14 @@
  *     Leverett-scaled Pc(Sw; phi) with Pc_ref,max / Pc_ref,min give the
  *     residual water / oil amounts, switched on by a hysteresis on the local
  *     normalised wetting density and counted separately from the lattice.
- *   - Constitutive curves: Kozeny-Carman K0(phi) (Appendix), Brooks-Corey
- *     Pc(Sw), Corey Kr(Sw).
+ *   - Constitutive curves: Kozeny-Carman K0(phi) (Appendix), Corey Kr(Sw),
+ *     and Pc(Sw) either Brooks-Corey or the Thomeer hyperbola the Appendix
+ *     fits (its coefficients are in the paper's ref. [12]; here the pore-
+ *     geometrical factor is an input).  Reading of the Thomeer form: the
+ *     normalised non-wetting saturation 1 - Se obeys
+ *     ln(1 - Se) log10(Pc / Pe) = -G with the entry pressure Pe = lamL Pd,
+ *     i.e. Pc = Pe 10^(-G / ln(1 - Se)), capped at 10 Pe (the cap the
+ *     Brooks-Corey clamp Se >= 1e-2 gives at lambda = 2).
  *
  *   - Pressure boundaries (the imbibition set-ups of Sec. I and the Appendix:
  *     a pressure difference between two boundaries of the domain, lowered in
@@ -83,6 +89,7 @@ typedef struct {
 
 typedef struct {
     double kc_d, pd, lambda, swr, nw, nn, phi_ref, f_max, f_min, aniso;
+    double thomeer_g; /* > 0: Thomeer Pc with this factor; 0: Brooks-Corey */
 } orc_curve;
 
 /* D3Q19 velocities: rest, the 6 faces, the 12 edges. */
@@ -199,22 +206,32 @@ static double leverett_factor(const orc_curve *cv, double phi)
     return sqrt((kref / cv->phi_ref) / (k / phi));
 }
 
-/* Water saturation on the Brooks-Corey curve Pc = lamL Pd Se^(-1/lambda)
- * at capillary pressure p (inverse of the curve; Se = 1 below entry). */
+/* Water saturation on the capillary-pressure curve at pressure p (the
+ * inverse of the curve, without its cap; Se = 1 at or below entry):
+ * Brooks-Corey Se = (p/Pe)^(-lambda); Thomeer 1 - Se = exp(-G / log10(p/Pe)). */
 static double sw_at_pressure(const orc_curve *cv, double lamL, double p)
 {
     double ratio = p / (lamL * cv->pd);
-    double se = pow(ratio, -cv->lambda);
+    double se;
+    if (cv->thomeer_g > 0.0)
+        se = ratio <= 1.0 ? 1.0 : 1.0 - exp(-cv->thomeer_g / log10(ratio));
+    else
+        se = pow(ratio, -cv->lambda);
     if (se > 1.0) se = 1.0;
     return cv->swr + (1.0 - cv->swr) * se;
 }
 
 static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-/* Brooks-Corey capillary pressure, Se clamped to [1e-2, 1]. */
+/* Capillary pressure, Se clamped to [1e-2, 1]: Brooks-Corey Pe Se^(-1/lambda),
+ * or Thomeer Pe 10^min(-G / ln(1 - Se), 1). */
 static double capillary_pressure(const orc_curve *cv, double lamL, double sw)
 {
     double se = clampd((sw - cv->swr) / (1.0 - cv->swr), 1e-2, 1.0);
+    if (cv->thomeer_g > 0.0) {
+        double e = -cv->thomeer_g / log(1.0 - se); /* 0 at se = 1 */
+        return lamL * cv->pd * pow(10.0, e < 1.0 ? e : 1.0);
+    }
     return lamL * cv->pd * pow(se, -1.0 / cv->lambda);
 }
 

@@ -16,7 +16,7 @@ DEFAULTS = dict(G=0.0, kappa=0.0, tau=(1.0, 1.0), accel=((0, 0, 0), (0, 0, 0)), 
                 s_lo=0.1, s_hi=0.9, at_cut=0.95, kr_min=1e-6, c_g=1.0, phi_avg=(0.515, 0.515),
                 phi_max=(1.0, 1.0), held=None)
 CURVE = dict(kc_d=1.0, pd=0.02, lam=2.0, swr=0.15, nw=3.0, nn=2.0, phi_ref=0.35, f_max=3.5,
-             f_min=0.575, aniso=1.0)
+             f_min=0.575, aniso=1.0, thomeer_g=0.0)
 
 
 class Case:
@@ -86,7 +86,8 @@ def run_gpu(case: Case, steps: int, device_arrays=False, path=0, tile=0, **extra
         for k, cv in enumerate(case.curves):
             lbm.lbm_set_constitutive(ctx, k, lbm.lbm_default_constitutive(
                 kc_d=cv["kc_d"], pd=cv["pd"], lam=cv["lam"], swr=cv["swr"], nw=cv["nw"], nn=cv["nn"],
-                phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"]))
+                phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"],
+                thomeer_g=cv["thomeer_g"]))
         if device_arrays:
             import torch
             dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -134,9 +135,11 @@ def droplet(n=32, R=8, kappa=0.0, csf_everywhere=0, tau=(1.0, 1.0), G=1.1):
                 csf_everywhere=csf_everywhere, tau=tau, probe=(c, c, c, R - 4, R + 4))
 
 
-def mixed_features(n=8, seed=5, shape=None, periodic=(1, 1, 1), aniso=10.0, flip_flags=True, tau=(0.8, 1.3)):
+def mixed_features(n=8, seed=5, shape=None, periodic=(1, 1, 1), aniso=10.0, flip_flags=True, tau=(0.8, 1.3),
+                   thomeer=0.0):
     """Solid, gray (two pore types, tensorial), walls with wetting densities,
-    CSF in gray cells, body forces, both residual transitions."""
+    CSF in gray cells, body forces, both residual transitions; thomeer > 0
+    gives the second pore type a Thomeer Pc curve with that factor."""
     rng = np.random.default_rng(seed)
     shape = shape or (n, n, n)
     cell = np.zeros(shape, np.uint8)
@@ -150,7 +153,7 @@ def mixed_features(n=8, seed=5, shape=None, periodic=(1, 1, 1), aniso=10.0, flip
     u0 = 0.01 * rng.standard_normal((3,) + shape)
     ptype = (rng.random(shape) < 0.5).astype(np.uint8)
     curves = [dict(CURVE, aniso=aniso), dict(CURVE, kc_d=1.5, pd=0.03, lam=1.5, swr=0.1, nw=2.5,
-                                            nn=1.5, aniso=3.0)]
+                                            nn=1.5, aniso=3.0, thomeer_g=thomeer)]
     return Case(f"mixed{shape}", shape, cell, phi, ra, rb, u=u0, ptype=ptype, curves=curves, G=1.1,
                 kappa=-0.045, tau=tau, accel=((1e-4, 2e-5, 0), (0, -1e-4, 3e-5)), rho_wall=(0.7, 0.2),
                 wet=1, periodic=periodic)
@@ -198,7 +201,7 @@ def imbibition(n=32, seed=synth.SEED_BASE + 6, dp=0.02, tau=(1.0, 1.0), nz=None)
                 tau=tau, rho_wall=(0.03, 1.0), wet=1, periodic=(1, 1, 0), held=held)
 
 
-def adjoint_case(n=8, seed=21, shape=None, steps_hint=None):
+def adjoint_case(n=8, seed=21, shape=None, steps_hint=None, thomeer=0.0):
     """Periodic lattice with solid, gray (one curve, tensorial, CSF, capillary)
     and both components, for the porosity gradient: A pushed along x."""
     rng = np.random.default_rng(seed)
@@ -210,5 +213,5 @@ def adjoint_case(n=8, seed=21, shape=None, steps_hint=None):
     zz, yy, xx = np.meshgrid(*(np.arange(s) for s in shape), indexing="ij")
     ra = np.where(xx < shape[2] // 2, 1.0, 0.03) + 0.02 * rng.random(shape)
     rb = 1.05 - ra
-    return Case(f"adjoint{shape}", shape, cell, phi, ra, rb, curves=[dict(CURVE, aniso=10.0)], G=1.1,
+    return Case(f"adjoint{shape}", shape, cell, phi, ra, rb, curves=[dict(CURVE, aniso=10.0, thomeer_g=thomeer)], G=1.1,
                 kappa=-0.045, tau=(0.8, 1.0), accel=((1e-4, 0, 0), (0, 0, 0)), rho_wall=(0.03, 1.0), wet=1)

@@ -111,7 +111,12 @@ def geometry(cell, phi_in, curve, c_g=1.0):
     lamL = np.sqrt((kref / curve["phi_ref"]) / (K0 / phis))
 
     def sw_at(p):
-        se = np.minimum((p / (lamL * curve["pd"])) ** (-curve["lambda"]), 1.0)
+        x = p / (lamL * curve["pd"])
+        if curve.get("thomeer_g", 0.0) > 0.0:
+            # Thomeer hyperbola: log10(x) ln(non-wetting fraction) = -G
+            se = np.where(x > 1.0, -np.expm1(-curve["thomeer_g"] / np.log10(np.where(x > 1.0, x, 2.0))), 1.0)
+        else:
+            se = np.minimum(x ** (-curve["lambda"]), 1.0)
         return curve["swr"] + (1 - curve["swr"]) * se
 
     swirr = sw_at(curve["f_max"] * curve["pd"])
@@ -237,7 +242,12 @@ class NaiveLBM:
         H = np.where(np.abs(At_field) <= p["at_cut"], 0.5 * mag, 0.0)
         cv = self.curve
         se_c = np.clip((sw - cv["swr"]) / (1 - cv["swr"]), 1e-2, 1.0)
-        Pc = self.geo["lamL"] * cv["pd"] * se_c ** (-1.0 / cv["lambda"])
+        if cv.get("thomeer_g", 0.0) > 0.0:
+            with np.errstate(divide="ignore"):
+                expo = np.minimum(cv["thomeer_g"] / -np.log1p(-se_c), 1.0)
+            Pc = self.geo["lamL"] * cv["pd"] * np.exp(np.log(10.0) * expo)
+        else:
+            Pc = self.geo["lamL"] * cv["pd"] * se_c ** (-1.0 / cv["lambda"])
         nvec = dAt / np.maximum(mag, p["eps_n"])
         for a in range(2):
             cap = -Pc[None] * (rho[a] / rt)[None] * nvec * H[None]

@@ -292,6 +292,18 @@ def test_capillary_force_flat_interface_telescopes():
     # Se^(-1/lambda) with lambda = 1e9 and Se >= 1e-2 keeps Pc within 5e-9 of pd
     assert abs(total - (-0.02 * jump)) < 1e-8 * 0.02
     assert np.abs(o.force_term(O.TERM_CAP, 0)[0]).max() < 1e-18
+    # Thomeer: Pc = Pe 10^(-G / ln(1 - Se)) tends to the entry pressure Pe as
+    # G -> 0 (|ln(1 - Se)| >= 0.01 for Se >= 1e-2) and, for Se < 1, is capped
+    # at 10 Pe (an amplitude 0.9 keeps s, hence Se, below 1 in every cell)
+    for g, scale, amp, tol in ((1e-9, 1.0, 0.99, 1e-6), (1e3, 10.0, 0.9, 1e-12)):
+        A = (-amp * np.cos(2 * np.pi * z / nz))[:, None, None] * np.ones(shape)
+        Az = A[:, 0, 0]
+        jump = 0.25 * (Az[b + 1] + Az[b] - Az[a] - Az[a - 1])
+        o = _rest_state(p, cell, 0.5 * c * (1 - A), 0.5 * c * (1 + A), phi=np.full(shape, 0.35),
+                        curves=[O.make_curve(thomeer_g=g, phi_ref=0.35)])
+        Fz = o.force_term(O.TERM_CAP, 0)[2] + o.force_term(O.TERM_CAP, 1)[2]
+        total = Fz[a:b + 1, 0, 0].sum()
+        assert abs(total - (-0.02 * scale * jump)) < tol * 0.02 * scale
 
 
 def test_csf_force_on_cylinder_matches_continuum():
@@ -471,6 +483,36 @@ def test_leverett_invariance_and_residual_crossings():
     assert np.any(st["sores"] == 0.0) and np.any(st["sores"] > 0.1)
 
 
+@pytest.mark.parametrize("g", [0.1, 0.4, 1.5])
+def test_thomeer_residual_crossings(g):
+    """Thomeer curve (the Appendix's Pc form): the residual amounts sit where
+    Thomeer's hyperbola log10(Pc/Pe) * ln(1 - Se) = -G crosses Pc_ref,max and
+    Pc_ref,min (Pe = lamL Pd, Se normalised); cells whose entry pressure is at
+    or above a reference pressure have Sw = 1 there; a larger G (more
+    gradual pore throats) leaves more residual water at the same pressure."""
+    n = 8
+    shape = (n, n, n)
+    rng = np.random.default_rng(4)
+    phi = 0.1 + 0.5 * rng.random(shape)
+    cell = np.full(shape, synth.GRAY, np.uint8)
+    cv = dict(pd=0.02, swr=0.15, phi_ref=0.35, f_max=3.5, f_min=0.575, thomeer_g=g)
+    st = O.Oracle(O.make_params(shape), cell, phi, curves=[O.make_curve(**cv)]).static()
+    for key, f in (("swirr", cv["f_max"]), ("sores", cv["f_min"])):
+        sw = st[key] if key == "swirr" else 1.0 - st[key]
+        x = f / st["lamL"]  # Pc_ref / Pe
+        below = x <= 1.0
+        assert np.all(sw[below] == 1.0)
+        se = (sw[~below] - cv["swr"]) / (1 - cv["swr"])
+        # 1 - Se is formed from Sw here, so cells just above entry, where the
+        # non-wetting fraction is tiny, are checked only for being tiny
+        ok = (1.0 - se) > 1e-5
+        np.testing.assert_allclose(np.log10(x[~below][ok]) * np.log(1.0 - se[ok]), -g, rtol=1e-9)
+        assert np.all(np.exp(-g / np.log10(x[~below][~ok])) <= 2e-5)
+    assert np.any(st["sores"] == 0.0) and np.any(st["sores"] > 0.0)
+    st2 = O.Oracle(O.make_params(shape), cell, phi, curves=[O.make_curve(**dict(cv, thomeer_g=2 * g))]).static()
+    assert np.all(st2["swirr"] >= st["swirr"]) and np.any(st2["swirr"] > st["swirr"])
+
+
 def test_residual_hysteresis_switches():
     """Wet cells with s < s_lo take residual water; dry cells with s > s_hi take residual oil."""
     n = 8
@@ -502,7 +544,7 @@ def test_residual_hysteresis_switches():
 # --------------------------------------------------------------------------
 # Brute force: the C oracle against the independent NumPy evaluator
 # --------------------------------------------------------------------------
-def _bruteforce_case(seed, csf_everywhere, tau, pressure=False):
+def _bruteforce_case(seed, csf_everywhere, tau, pressure=False, thomeer=0.0):
     rng = np.random.default_rng(seed)
     n = 8
     shape = (n, n, n)
@@ -524,7 +566,7 @@ def _bruteforce_case(seed, csf_everywhere, tau, pressure=False):
     common = dict(G=1.1, kappa=-0.045, tau=tau, accel=((1e-4, 2e-5, 0), (0, -1e-4, 3e-5)),
                   c_g=1.0, rho_wall=(0.7, 0.2), wet=1, csf_everywhere=csf_everywhere, **bc)
     curve = dict(kc_d=1.0, pd=0.02, swr=0.15, nw=3.0, nn=2.0, phi_ref=0.35, f_max=3.5,
-                 f_min=0.575, aniso=10.0)
+                 f_min=0.575, aniso=10.0, thomeer_g=thomeer)
     o = O.Oracle(O.make_params(shape, **common), cell, phi, curves=[O.make_curve(lam=2.0, **curve)])
     pd = dict(common, rho_hi=1.0, rho_lo=0.03, phi_avg=(0.515, 0.515), phi_max=(1.0, 1.0),
               s_lo=0.1, s_hi=0.9, at_cut=0.95, eps_n=1e-4, kr_min=1e-6)
@@ -539,10 +581,12 @@ def _bruteforce_case(seed, csf_everywhere, tau, pressure=False):
     return o, nv, cell
 
 
-@pytest.mark.parametrize("csf_everywhere,tau,pressure", [(0, (0.8, 1.3), False), (1, (1.0, 1.0), False),
-                                                         (0, (0.8, 1.3), True)])
-def test_bruteforce_against_numpy_evaluator(csf_everywhere, tau, pressure):
-    o, nv, cell = _bruteforce_case(5, csf_everywhere, tau, pressure)
+@pytest.mark.parametrize("csf_everywhere,tau,pressure,thomeer", [(0, (0.8, 1.3), False, 0.0),
+                                                                 (1, (1.0, 1.0), False, 0.0),
+                                                                 (0, (0.8, 1.3), True, 0.0),
+                                                                 (0, (0.8, 1.3), False, 0.35)])
+def test_bruteforce_against_numpy_evaluator(csf_everywhere, tau, pressure, thomeer):
+    o, nv, cell = _bruteforce_case(5, csf_everywhere, tau, pressure, thomeer)
     st = o.static()
     np.testing.assert_allclose(np.moveaxis(st["kinv"], (0, 1), (-2, -1)), nv.geo["kinv"],
                                rtol=1e-12, atol=0)
