@@ -126,7 +126,11 @@ typedef struct lbm_params {
 /* Constitutive curves of one pore type (Appendix: Kozeny-Carman K0,
  * capillary pressure and Corey relative permeabilities; Eq. 5 scaling).
  *   K0(phi)  = kc_d^2 phi^3 / (180 (1 - phi)^2)
- *   Pc(Sw)   = lamL(phi) pd Se^(-1/lambda),  Se = (Sw - swr)/(1 - swr) in [1e-2, 1]
+ *   Pc(Sw)   = Pe Se^(-1/lambda) (Brooks-Corey, thomeer_g = 0), or
+ *              Pe 10^min(-thomeer_g / ln(1 - Se), 1) (Thomeer's hyperbola
+ *              log10(Pc/Pe) ln(1 - Se) = -G, the form the Appendix fits,
+ *              capped at 10 Pe), with Pe = lamL(phi) pd and
+ *              Se = (Sw - swr)/(1 - swr) in [1e-2, 1]
  *   lamL     = sqrt((K0(phi_ref)/phi_ref) / (K0(phi)/phi))        (Leverett)
  *   Kr_w     = Se^nw,  Kr_n = (1 - Se)^nn                          (Se in [0, 1])
  *   residual water Sw_irr = Sw at Pc = pc_ref_max_f * pd; residual oil
@@ -135,6 +139,7 @@ typedef struct lbm_params {
  *              K^D = diag(K0/a, K0, K0) along the principal axis e1. */
 typedef struct lbm_constitutive {
     double kc_d, pd, lambda, swr, nw, nn, phi_ref, pc_ref_max_f, pc_ref_min_f, aniso;
+    double thomeer_g; /* Thomeer pore-geometrical factor G > 0, or 0 for Brooks-Corey */
 } lbm_constitutive;
 
 /* Observables of the current fields (FP64 reductions). */

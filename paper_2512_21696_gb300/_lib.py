@@ -57,7 +57,7 @@ class lbm_params(C.Structure):
 
 class lbm_constitutive(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("kc_d", "pd", "lambda_", "swr", "nw", "nn", "phi_ref",
-                                          "pc_ref_max_f", "pc_ref_min_f", "aniso")]
+                                          "pc_ref_max_f", "pc_ref_min_f", "aniso", "thomeer_g")]
 
 
 class lbm_obs(C.Structure):

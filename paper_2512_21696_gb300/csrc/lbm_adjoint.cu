@@ -39,6 +39,34 @@ struct AdjSeed {
 
 __device__ __forceinline__ float adj_phi_c(uint8_t t, float ph) { return t == CELL_GRAY ? ph : 1.0f; }
 
+// Pc / Pe of a curve at the clamped normalised saturation se and its
+// derivative in se: Brooks-Corey se^(-1/lambda); Thomeer
+// 2^min(k / log2(1 - se), log2 10) (derivative pw k / (log2(1 - se)^2 (1 - se))
+// below the cap, 0 on it; 1 with derivative 0 at se = 1, where the clamp
+// stops the adjoint anyway).
+__device__ __forceinline__ float pc_shape(const Curve &cv, float se, float &dpw)
+{
+    if (cv.thomeer_k != 0.f) {
+        const float om = 1.f - se;
+        if (!(om > 0.f)) {
+            dpw = 0.f;
+            return 1.f;
+        }
+        const float L = log2f(om);
+        const float E = cv.thomeer_k / L;
+        if (E >= LOG2_10) {
+            dpw = 0.f;
+            return 10.f;
+        }
+        const float pw = exp2f(E);
+        dpw = pw * cv.thomeer_k / (L * L * om);
+        return pw;
+    }
+    const float pw = powf(se, cv.neg_inv_lambda);
+    dpw = cv.neg_inv_lambda * pw / se;
+    return pw;
+}
+
 template <int N>
 __device__ __forceinline__ float dotn(const float *a, const float *b)
 {
@@ -201,7 +229,8 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
         Hh = (fabsf(At_c) <= P.at_cut) ? 0.5f * mag : 0.f;
         if (Hh > 0.f) {
             se_c = fminf(fmaxf((sw - cv.swr) * cv.inv_1m_swr, 1e-2f), 1.f);
-            Pc = pcs * powf(se_c, cv.neg_inv_lambda);
+            float pw_unused;
+            Pc = pcs * pc_shape(cv, se_c, pw_unused);
             mden = fmaxf(mag, P.eps_n);
             kcap = -Pc * Hh / (mden * rt);
             for (int a = 0; a < 2; ++a)
@@ -358,10 +387,11 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
             const float lmag = 0.5f * lHh + (mag > P.eps_n ? lm : 0.f);
             if (mag > 0.f)
                 for (int d = 0; d < 3; ++d) lgat[d] += lmag * gAt[d] / mag;
-            // Pc = pcs se_c^(-1/lambda)
-            const float pw = powf(se_c, cv.neg_inv_lambda);
+            // Pc = pcs pw(se_c)
+            float dpw;
+            const float pw = pc_shape(cv, se_c, dpw);
             lgk[1] += lPc * pw;
-            const float lsec = lPc * pcs * cv.neg_inv_lambda * pw / se_c;
+            const float lsec = lPc * pcs * dpw;
             const float sec_raw = (sw - cv.swr) * cv.inv_1m_swr;
             if (sec_raw > 1e-2f && sec_raw < 1.f) lsw += lsec * cv.inv_1m_swr;
             for (int i = 1; i < Q; ++i)
@@ -557,10 +587,21 @@ __global__ void k_geom_adjoint(DevParams P, CurveTableA T, double c_g, const uin
     // lamL^2 = C phi / K0  ->  dlamL = lamL/2 (1/phi - K0'/K0)
     const double dlam = 0.5 * lamL * (1.0 / ph - dK0 / K0);
     double g = gk[3] * (-dK0 / (K0 * K0)) + gk[4] * cv.pd * dlam;
-    // Sw(f) = swr + (1 - swr) min(1, (f/lamL)^-lambda) = ... (lamL/f)^lambda
-    const double semax = pow(cv.pc_ref_max_f / lamL, -cv.lambda), semin = pow(cv.pc_ref_min_f / lamL, -cv.lambda);
-    if (semax < 1.0) g += gk[5] * (1.0 - cv.swr) * cv.lambda * semax / lamL * dlam;
-    if (semin < 1.0) g += -gk[6] * (1.0 - cv.swr) * cv.lambda * semin / lamL * dlam;
+    // Sw(f) = swr + (1 - swr) Se(x), x = f / lamL: Brooks-Corey Se = min(1, x^-lambda),
+    // dSe/dlamL = lambda Se / lamL below 1; Thomeer Se = 1 - exp(-G/u), u = log10 x,
+    // dSe/dlamL = exp(-G/u) G / (u^2 lamL ln 10) above entry; 0 where Se = 1
+    auto dse_dlam = [&](double f) {
+        const double x = f / lamL;
+        if (cv.thomeer_g > 0.0) {
+            if (x <= 1.0) return 0.0;
+            const double u = log10(x), e = exp(-cv.thomeer_g / u);
+            return e * cv.thomeer_g / (u * u * lamL * log(10.0));
+        }
+        const double se = pow(x, -cv.lambda);
+        return se < 1.0 ? cv.lambda * se / lamL : 0.0;
+    };
+    g += gk[5] * (1.0 - cv.swr) * dse_dlam(cv.pc_ref_max_f) * dlam;
+    g += -gk[6] * (1.0 - cv.swr) * dse_dlam(cv.pc_ref_min_f) * dlam;
     atomicAdd(&dphi[c], g);
     // principal axis: v = sqrt(a - 1) e1(M), M = H H + c_g grad grad^T
     const double lv2 = gk[0] * gk[0] + gk[1] * gk[1] + gk[2] * gk[2];

@@ -34,7 +34,7 @@ bool valid_curve(const lbm_constitutive &c)
 {
     return c.kc_d > 0 && c.pd > 0 && c.lambda > 0 && c.swr >= 0 && c.swr < 1 && c.nw > 0 && c.nn > 0 &&
            c.phi_ref > 0 && c.phi_ref < 1 && c.pc_ref_max_f > 0 && c.pc_ref_min_f > 0 && c.aniso >= 1 &&
-           std::isfinite(c.aniso);
+           std::isfinite(c.aniso) && c.thomeer_g >= 0 && std::isfinite(c.thomeer_g);
 }
 
 // Bytes of one population buffer: 2 components x 19 slots x n cells.
@@ -97,6 +97,8 @@ void fill_device_params(lbm_ctx *ctx)
         d.curve[k].neg_inv_lambda = (float)(-1.0 / c.lambda);
         d.curve[k].nw = (float)c.nw;
         d.curve[k].nn = (float)c.nn;
+        // Thomeer: 10^(-G / ln(1 - Se)) = 2^(k / log2(1 - Se)), k = -G log2(10) / ln 2
+        d.curve[k].thomeer_k = c.thomeer_g > 0 ? (float)(-c.thomeer_g * std::log2(10.0) / std::log(2.0)) : 0.0f;
     }
 }
 
@@ -243,6 +245,7 @@ int lbm_default_constitutive(lbm_constitutive *c)
     c->pc_ref_max_f = 3.5;
     c->pc_ref_min_f = 0.575;
     c->aniso = 1.0;
+    c->thomeer_g = 0.0;
     return LBM_OK;
 }
 

@@ -557,7 +557,11 @@ __device__ __forceinline__ void collide_store(const DevParams &P, const float (&
         const float H = (fabsf(At_c) <= P.at_cut) ? 0.5f * mag : 0.f;
         if (H > 0.f) {
             const float se_c = fminf(fmaxf((sw - cv.swr) * cv.inv_1m_swr, 1e-2f), 1.f);
-            const float Pc = gb.x * __powf(se_c, cv.neg_inv_lambda);
+            // Pc / Pe: Brooks-Corey Se^(-1/lambda), or Thomeer
+            // 10^min(-G / ln(1 - Se), 1) = 2^min(k / log2(1 - Se), log2 10) (1 at Se = 1)
+            const float pw = cv.thomeer_k != 0.f ? exp2f(fminf(cv.thomeer_k / __log2f(1.f - se_c), LOG2_10))
+                                                 : __powf(se_c, cv.neg_inv_lambda);
+            const float Pc = gb.x * pw;
             const float k = __fdividef(-Pc * H, fmaxf(mag, P.eps_n)) * irt;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {

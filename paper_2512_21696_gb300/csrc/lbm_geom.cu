@@ -137,8 +137,15 @@ __global__ void k_geometry(DevParams P, CurveTable T, double c_g, const uint8_t 
     const double K0 = kozeny(cv, ph);
     const double kref = kozeny(cv, cv.phi_ref);
     const double lamL = sqrt((kref / cv.phi_ref) / (K0 / ph));
-    const double se_max = fmin(pow(cv.pc_ref_max_f / lamL, -cv.lambda), 1.0);
-    const double se_min = fmin(pow(cv.pc_ref_min_f / lamL, -cv.lambda), 1.0);
+    // Se where the curve crosses f Pd, x = f / lamL = Pc / Pe: Brooks-Corey
+    // x^(-lambda); Thomeer 1 - exp(-G / log10 x) above entry; 1 at or below entry
+    auto se_at = [&](double f) {
+        const double x = f / lamL;
+        if (cv.thomeer_g > 0.0) return x <= 1.0 ? 1.0 : 1.0 - exp(-cv.thomeer_g / log10(x));
+        return fmin(pow(x, -cv.lambda), 1.0);
+    };
+    const double se_max = se_at(cv.pc_ref_max_f);
+    const double se_min = se_at(cv.pc_ref_min_f);
     const double sw_irr = cv.swr + (1.0 - cv.swr) * se_max;
     const double so_res = 1.0 - (cv.swr + (1.0 - cv.swr) * se_min);
     GrayRec rec;

@@ -17,7 +17,8 @@ def _ctx(case):
     cv = case.curves[0]
     lbm.lbm_set_constitutive(ctx, 0, lbm.lbm_default_constitutive(
         kc_d=cv["kc_d"], pd=cv["pd"], lam=cv["lam"], swr=cv["swr"], nw=cv["nw"], nn=cv["nn"],
-        phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"]))
+        phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"],
+        thomeer_g=cv.get("thomeer_g", 0.0)))
     return ctx
 
 
@@ -40,9 +41,9 @@ def _oracle_grad(case, steps):
                                case.rhoA32.astype(np.float64), case.rhoB32.astype(np.float64), steps, *TARGETS)
 
 
-@pytest.mark.parametrize("steps,ckpt", [(6, 4), (40, 16)])
-def test_adjoint_matches_oracle_discrete_adjoint(steps, ckpt):
-    case = LC.adjoint_case()
+@pytest.mark.parametrize("steps,ckpt,thomeer", [(6, 4, 0.0), (40, 16, 0.0), (40, 16, 0.3)])
+def test_adjoint_matches_oracle_discrete_adjoint(steps, ckpt, thomeer):
+    case = LC.adjoint_case(thomeer=thomeer)
     L, q, S, g, _ = _gpu_grad(case, steps, ckpt)
     Lo, qo, So, go = _oracle_grad(case, steps)
     gray = case.cell == synth.GRAY

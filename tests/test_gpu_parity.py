@@ -54,6 +54,17 @@ def test_mixed_features_small(steps, path, tile):
     _compare(case, gf, of)
 
 
+@pytest.mark.parametrize("path,tile", [(0, 2), (1, 0)])
+def test_mixed_features_thomeer_curve(path, tile):
+    """The second pore type on a Thomeer Pc curve (capillary force, residual
+    crossings of the geometry precompute)."""
+    case = LC.mixed_features(thomeer=0.35, seed=11)
+    gf, _, gst = LC.run_gpu(case, 10, path=path, tile=tile)
+    of, _, ost = LC.run_oracle(case, 10)
+    _compare_static(case, gst, ost)
+    _compare(case, gf, of)
+
+
 def test_mixed_features_device_arrays_and_tau():
     case = LC.mixed_features(seed=7, tau=(0.55, 0.7))
     gf, _, _ = LC.run_gpu(case, 20, device_arrays=True)
@@ -180,7 +191,8 @@ def test_checkpoint_roundtrip_is_bit_exact():
         for k, cv in enumerate(case.curves):
             lbm.lbm_set_constitutive(ctx, k, lbm.lbm_default_constitutive(
                 kc_d=cv["kc_d"], pd=cv["pd"], lam=cv["lam"], swr=cv["swr"], nw=cv["nw"], nn=cv["nn"],
-                phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"]))
+                phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"],
+        thomeer_g=cv.get("thomeer_g", 0.0)))
         lbm.lbm_set_geometry(ctx, case.cell, case.phi32, case.ptype)
         lbm.lbm_init_fields(ctx, case.rhoA32, case.rhoB32, case.u32)
         lbm.lbm_step(ctx, 7)

@@ -36,7 +36,8 @@ def _setup(ctx, case):
     for k, cv in enumerate(case.curves):
         lbm.lbm_set_constitutive(ctx, k, lbm.lbm_default_constitutive(
             kc_d=cv["kc_d"], pd=cv["pd"], lam=cv["lam"], swr=cv["swr"], nw=cv["nw"], nn=cv["nn"],
-            phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"]))
+            phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"],
+        thomeer_g=cv.get("thomeer_g", 0.0)))
     lbm.lbm_set_geometry(ctx, case.cell, case.phi32, case.ptype)
     lbm.lbm_init_fields(ctx, case.rhoA32, case.rhoB32, case.u32)
     lbm.lbm_set_pressure(ctx, *case.s["held"])
