@@ -44,6 +44,7 @@ class OrcParams(C.Structure):
         ("s_lo", C.c_double), ("s_hi", C.c_double), ("at_cut", C.c_double),
         ("eps_n", C.c_double), ("kr_min", C.c_double), ("c_g", C.c_double),
         ("rho_in", C.c_double * 2), ("rho_out", C.c_double * 2),
+        ("lattice", C.c_int),
     ]
 
 
@@ -91,6 +92,8 @@ def _load():
         lib.orc_collide_cell.argtypes = [dp, dp, dp, C.c_double, dp]
         lib.orc_set_threads.argtypes = [C.c_int]
         lib.orc_max_threads.restype = C.c_int
+        lib.orc_q.restype = C.c_int
+        lib.orc_q.argtypes = [P]
         lib.orc_steps.restype = C.c_long
         lib.orc_steps.argtypes = [P]
         _lib = lib
@@ -147,6 +150,7 @@ def make_params(shape, **kw) -> OrcParams:
     p.eps_n = kw.pop("eps_n", 1e-4 * rho_hi)
     p.kr_min = kw.pop("kr_min", 1e-6)
     p.c_g = kw.pop("c_g", 1.0)
+    p.lattice = {"d3q19": 0, "d2q9": 1}[kw.pop("lattice", "d3q19")]
     rin = kw.pop("rho_in", (rho_hi, rho_lo))
     rout = kw.pop("rho_out", (rho_hi, rho_lo))
     for a in range(2):
@@ -187,6 +191,7 @@ class Oracle:
         if not self._h:
             raise RuntimeError("orc_create failed")
         self.cell = cell
+        self.Q = int(self.lib.orc_q(self._h))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -249,13 +254,13 @@ class Oracle:
                                   np.asarray(rho_out, dtype=np.float64))
 
     def populations(self):
-        f = np.zeros(38 * self.n)
+        f = np.zeros(2 * self.Q * self.n)
         self.lib.orc_get_populations(self._h, f)
-        return f.reshape((2, 19) + self.shape)
+        return f.reshape((2, self.Q) + self.shape)
 
     def set_populations(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
-        assert f.size == 38 * self.n
+        assert f.size == 2 * self.Q * self.n
         self.lib.orc_set_populations(self._h, f)
 
     def residual(self):

@@ -1,6 +1,7 @@
 /*
  * FP64 CPU oracle of the two-component pseudo-potential lattice Boltzmann
- * step on D3Q19 with the multiscale models of arXiv 2512.21696.
+ * step on D3Q19 (and, for the paper's two-dimensional experiments of
+ * Sec. III, on D2Q9) with the multiscale models of arXiv 2512.21696.
  *
  * TEST INFRASTRUCTURE ONLY.  The tests, the smoke check and the CPU-baseline
  * leg of the benchmark call this file; the library path never does.  It shares
@@ -53,6 +54,11 @@
  *     streams into the domain.  The pressure of a reservoir is
  *     p = cs^2 (rhoA + rhoB) + G rhoA rhoB.
  *
+ *   - D2Q9: the same step on one plane with the nine-velocity set (weights
+ *     4/9, 1/9, 1/36, cs^2 = 1/3); every formula above is written for
+ *     three-component vectors whose z parts vanish, and the identity in the
+ *     density Hessian of Eq. 4 is that of the plane.
+ *
  * Order inside one step: stream; moments at all cells; residual update;
  * density gradients at all cells; forces and velocity; collide.
  * Every force reads neighbour densities of the same time level.
@@ -85,6 +91,7 @@ typedef struct {
     double rho_hi, rho_lo;
     double s_lo, s_hi, at_cut, eps_n, kr_min, c_g;
     double rho_in[2], rho_out[2]; /* densities held in inlet / outlet cells */
+    int lattice;                  /* 0: D3Q19; 1: D2Q9 (nz = 1) */
 } orc_params;
 
 typedef struct {
@@ -93,32 +100,50 @@ typedef struct {
 } orc_curve;
 
 /* D3Q19 velocities: rest, the 6 faces, the 12 edges. */
-static const int CV[19][3] = {
+static const int CV19[19][3] = {
     {0, 0, 0},
     {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
     {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},
     {1, 0, 1}, {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
     {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+/* D2Q9 velocities (the plane z = 0): rest, the 4 faces, the 4 diagonals. */
+static const int CV9[9][3] = {
+    {0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+    {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
 
 static const double CS2 = 1.0 / 3.0;
 
-static double weight(int i)
-{
-    int len2 = CV[i][0] * CV[i][0] + CV[i][1] * CV[i][1] + CV[i][2] * CV[i][2];
-    if (len2 == 0) return 1.0 / 3.0;
-    if (len2 == 1) return 1.0 / 18.0;
-    return 1.0 / 36.0;
-}
+/* A velocity set: Q velocities in `dim` dimensions (z components zero in 2-D),
+ * their weights and opposites.  Both sets have cs^2 = 1/3. */
+typedef struct {
+    int Q, dim;
+    int cv[19][3];
+    double w[19];
+    int opp[19];
+} lattice;
 
-static int opposite(int i)
+static void make_lattice(lattice *L, int d2q9)
 {
-    for (int k = 0; k < 19; ++k)
-        if (CV[k][0] == -CV[i][0] && CV[k][1] == -CV[i][1] && CV[k][2] == -CV[i][2]) return k;
-    return -1;
+    L->Q = d2q9 ? 9 : 19;
+    L->dim = d2q9 ? 2 : 3;
+    for (int i = 0; i < L->Q; ++i)
+        for (int d = 0; d < 3; ++d) L->cv[i][d] = d2q9 ? CV9[i][d] : CV19[i][d];
+    for (int i = 0; i < L->Q; ++i) {
+        int len2 = L->cv[i][0] * L->cv[i][0] + L->cv[i][1] * L->cv[i][1] + L->cv[i][2] * L->cv[i][2];
+        if (d2q9)
+            L->w[i] = len2 == 0 ? 4.0 / 9.0 : (len2 == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+        else
+            L->w[i] = len2 == 0 ? 1.0 / 3.0 : (len2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+        L->opp[i] = -1;
+        for (int k = 0; k < L->Q; ++k)
+            if (L->cv[k][0] == -L->cv[i][0] && L->cv[k][1] == -L->cv[i][1] && L->cv[k][2] == -L->cv[i][2])
+                L->opp[i] = k;
+    }
 }
 
 typedef struct orc_state {
     orc_params p;
+    lattice L;
     long n;
     uint8_t *type, *ptype;
     double *phi;
@@ -277,18 +302,21 @@ static void jacobi3(double A[3][3], double evals[3], double V[3][3])
 
 /* Hessian of the density of component a at fluid cell c from the lattice
  * moments: since sum_i w_i (c_i c_i - cs^2 I) c_i c_i : X = 2 cs^4 X for
- * symmetric X on D3Q19, H = (1/cs^4) sum_i w_i (c_i c_i - cs^2 I)
- * (rho(x + c_i) - rho(x)), solid neighbours carrying rho_wall. */
+ * symmetric X on D3Q19 (and on D2Q9 in its plane), H = (1/cs^4) sum_i w_i
+ * (c_i c_i - cs^2 I) (rho(x + c_i) - rho(x)), I the identity of the lattice's
+ * dimensions, solid neighbours carrying rho_wall. */
 static void density_hessian(const orc_state *st, long c, int a, double H[3][3])
 {
+    const lattice *L = &st->L;
     double fc = st->rho[a][c];
     for (int d = 0; d < 3; ++d)
         for (int e = 0; e < 3; ++e) H[d][e] = 0.0;
-    for (int i = 1; i < 19; ++i) {
-        double df = rho_seen(st, neighbour(st, c, CV[i][0], CV[i][1], CV[i][2]), a) - fc;
+    for (int i = 1; i < L->Q; ++i) {
+        double df = rho_seen(st, neighbour(st, c, L->cv[i][0], L->cv[i][1], L->cv[i][2]), a) - fc;
         for (int d = 0; d < 3; ++d)
             for (int e = 0; e < 3; ++e)
-                H[d][e] += weight(i) * (CV[i][d] * CV[i][e] - (d == e ? CS2 : 0.0)) * df / (CS2 * CS2);
+                H[d][e] += L->w[i] * (L->cv[i][d] * L->cv[i][e] - (d == e && d < L->dim ? CS2 : 0.0)) * df /
+                           (CS2 * CS2);
     }
 }
 
@@ -297,12 +325,13 @@ static void gray_static(orc_state *st, long c)
 {
     const orc_curve *cv = &st->curve[st->ptype[c]];
     double phi = st->phi[c];
-    /* gradient with the isotropic D3Q19 stencil */
+    /* gradient with the isotropic stencil of the lattice */
+    const lattice *L = &st->L;
     double g[3] = {0, 0, 0};
-    for (int i = 0; i < 19; ++i) {
-        long m = neighbour(st, c, CV[i][0], CV[i][1], CV[i][2]);
+    for (int i = 0; i < L->Q; ++i) {
+        long m = neighbour(st, c, L->cv[i][0], L->cv[i][1], L->cv[i][2]);
         double v = phi_seen(st, m);
-        for (int d = 0; d < 3; ++d) g[d] += weight(i) * v * CV[i][d] / CS2;
+        for (int d = 0; d < 3; ++d) g[d] += L->w[i] * v * L->cv[i][d] / CS2;
     }
     /* Hessian: second differences on the faces, four-point cross terms */
     double H[3][3];
@@ -364,48 +393,58 @@ static void gray_static(orc_state *st, long c)
 /* ---------------------------------------------------------------------- */
 /* Collision of one component at one cell                                  */
 /* ---------------------------------------------------------------------- */
-static void equilibrium(double rho, const double u[3], double feq[19])
+static void equilibrium(const lattice *L, double rho, const double u[3], double feq[19])
 {
     double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    for (int i = 0; i < 19; ++i) {
-        double cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
-        feq[i] = weight(i) * rho * (1.0 + cu / CS2 + (cu * cu - CS2 * uu) / (2.0 * CS2 * CS2));
+    for (int i = 0; i < L->Q; ++i) {
+        double cu = L->cv[i][0] * u[0] + L->cv[i][1] * u[1] + L->cv[i][2] * u[2];
+        feq[i] = L->w[i] * rho * (1.0 + cu / CS2 + (cu * cu - CS2 * uu) / (2.0 * CS2 * CS2));
     }
 }
 
-/* Eq. 3 force term F_i for force F at velocity u. */
-static double force_term(int i, const double u[3], const double F[3])
+/* Eq. 3 force term F_i for force F at velocity u (in 2-D, u and F have no
+ * z component, so the zz entry of c c - cs^2 I meets zeros). */
+static double force_term(const lattice *L, int i, const double u[3], const double F[3])
 {
     double cF = 0.0, sec = 0.0;
-    for (int a = 0; a < 3; ++a) cF += CV[i][a] * F[a];
+    for (int a = 0; a < 3; ++a) cF += L->cv[i][a] * F[a];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
-            double Q = CV[i][a] * CV[i][b] - (a == b ? CS2 : 0.0);
+            double Q = L->cv[i][a] * L->cv[i][b] - (a == b ? CS2 : 0.0);
             sec += (u[a] * F[b] + F[a] * u[b]) * Q;
         }
-    return weight(i) * (cF / CS2 + sec / (2.0 * CS2 * CS2));
+    return L->w[i] * (cF / CS2 + sec / (2.0 * CS2 * CS2));
 }
 
-void orc_collide_cell(const double fin[19], const double u[3], const double F[3], double tau,
-                      double fout[19])
+static void collide_cell(const lattice *L, const double *fin, const double u[3], const double F[3], double tau,
+                         double *fout)
 {
     double rho = 0.0;
-    for (int i = 0; i < 19; ++i) rho += fin[i];
+    for (int i = 0; i < L->Q; ++i) rho += fin[i];
     double feq[19];
-    equilibrium(rho, u, feq);
+    equilibrium(L, rho, u, feq);
     double P[3][3];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
             double acc = 0.0;
-            for (int i = 0; i < 19; ++i) acc += CV[i][a] * CV[i][b] * (fin[i] - feq[i]);
+            for (int i = 0; i < L->Q; ++i) acc += L->cv[i][a] * L->cv[i][b] * (fin[i] - feq[i]);
             P[a][b] = acc + 0.5 * (u[a] * F[b] + F[a] * u[b]);
         }
-    for (int i = 0; i < 19; ++i) {
+    for (int i = 0; i < L->Q; ++i) {
         double QP = 0.0;
         for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) QP += (CV[i][a] * CV[i][b] - (a == b ? CS2 : 0.0)) * P[a][b];
-        fout[i] = feq[i] + (1.0 - 1.0 / tau) * weight(i) * QP / (2.0 * CS2 * CS2) + 0.5 * force_term(i, u, F);
+            for (int b = 0; b < 3; ++b) QP += (L->cv[i][a] * L->cv[i][b] - (a == b ? CS2 : 0.0)) * P[a][b];
+        fout[i] = feq[i] + (1.0 - 1.0 / tau) * L->w[i] * QP / (2.0 * CS2 * CS2) + 0.5 * force_term(L, i, u, F);
     }
+}
+
+/* One D3Q19 cell (exported for the moment-identity tests). */
+void orc_collide_cell(const double fin[19], const double u[3], const double F[3], double tau,
+                      double fout[19])
+{
+    lattice L;
+    make_lattice(&L, 0);
+    collide_cell(&L, fin, u, F, tau, fout);
 }
 
 /* Solve A x = b (3x3) by Gaussian elimination with partial pivoting. */
@@ -480,8 +519,11 @@ orc_state *orc_create(const orc_params *p, const orc_curve *curves, int ncurve,
                       const uint8_t *type, const double *phi, const uint8_t *ptype)
 {
     if (ncurve < 1 || ncurve > ORC_MAX_TYPES) return NULL;
+    if (p->lattice == 1 && p->nz != 1) return NULL;
     orc_state *st = (orc_state *)calloc(1, sizeof(orc_state));
     st->p = *p;
+    make_lattice(&st->L, p->lattice == 1);
+    if (p->lattice == 1) st->p.periodic[2] = 1; /* one plane: z-invariant stencils */
     st->n = (long)p->nx * p->ny * p->nz;
     long n = st->n;
     st->ncurve = ncurve;
@@ -498,8 +540,8 @@ orc_state *orc_create(const orc_params *p, const orc_curve *curves, int ncurve,
     st->iso = (int *)calloc((size_t)n, sizeof(int));
     st->Rw = alloc0(n); st->Ro = alloc0(n);
     st->wetflag = (int *)calloc((size_t)n, sizeof(int));
-    st->f = alloc0(2 * 19 * n);
-    st->fs = alloc0(2 * 19 * n);
+    st->f = alloc0(2 * (long)st->L.Q * n);
+    st->fs = alloc0(2 * (long)st->L.Q * n);
     for (int a = 0; a < 2; ++a) {
         st->rho[a] = alloc0(n); st->grad[a] = alloc0(3 * n);
         st->F[a] = alloc0(3 * n);
@@ -539,8 +581,9 @@ void orc_init_fields(orc_state *st, const double *rhoA, const double *rhoB, cons
         double r[2] = {rhoA[c], rhoB[c]};
         for (int a = 0; a < 2; ++a) {
             double feq[19];
-            equilibrium(r[a], uc, feq);
-            for (int i = 0; i < 19; ++i) st->f[((long)a * 19 + i) * n + c] = st->type[c] == SOLID ? 0.0 : feq[i];
+            const int Q = st->L.Q;
+            equilibrium(&st->L, r[a], uc, feq);
+            for (int i = 0; i < Q; ++i) st->f[((long)a * Q + i) * n + c] = st->type[c] == SOLID ? 0.0 : feq[i];
             st->rho[a][c] = st->type[c] == SOLID ? 0.0 : r[a];
         }
         for (int d = 0; d < 3; ++d) st->u[d * n + c] = st->type[c] == SOLID ? 0.0 : uc[d];
@@ -567,8 +610,10 @@ void orc_set_pressure(orc_state *st, const double rho_in[2], const double rho_ou
     }
 }
 
-void orc_set_populations(orc_state *st, const double *f) { memcpy(st->f, f, sizeof(double) * 38 * (size_t)st->n); }
-void orc_get_populations(const orc_state *st, double *f) { memcpy(f, st->f, sizeof(double) * 38 * (size_t)st->n); }
+/* Populations [2][Q][n] (Q = 19 or 9). */
+void orc_set_populations(orc_state *st, const double *f) { memcpy(st->f, f, sizeof(double) * 2 * st->L.Q * (size_t)st->n); }
+void orc_get_populations(const orc_state *st, double *f) { memcpy(f, st->f, sizeof(double) * 2 * st->L.Q * (size_t)st->n); }
+int orc_q(const orc_state *st) { return st->L.Q; }
 void orc_set_residual(orc_state *st, const double *Rw, const double *Ro, const int *wet)
 {
     memcpy(st->Rw, Rw, sizeof(double) * (size_t)st->n);
@@ -590,8 +635,9 @@ static void one_step(orc_state *st)
     const long n = st->n;
     const orc_params *p = &st->p;
     const int w = p->wet;
-    int opp[19];
-    for (int i = 0; i < 19; ++i) opp[i] = opposite(i);
+    const lattice *L = &st->L;
+    const int Q = L->Q;
+    const int *opp = L->opp;
 
     /* (1) streaming with halfway bounce-back, (2) moments */
 #pragma omp parallel for schedule(static)
@@ -600,13 +646,13 @@ static void one_step(orc_state *st)
         double jc[3] = {0, 0, 0};
         for (int a = 0; a < 2; ++a) {
             double r = 0.0;
-            for (int i = 0; i < 19; ++i) {
-                long src = neighbour(st, c, -CV[i][0], -CV[i][1], -CV[i][2]);
-                double v = is_wall(st, src) ? st->f[((long)a * 19 + opp[i]) * n + c]
-                                            : st->f[((long)a * 19 + i) * n + src];
-                st->fs[((long)a * 19 + i) * n + c] = v;
+            for (int i = 0; i < Q; ++i) {
+                long src = neighbour(st, c, -L->cv[i][0], -L->cv[i][1], -L->cv[i][2]);
+                double v = is_wall(st, src) ? st->f[((long)a * Q + opp[i]) * n + c]
+                                            : st->f[((long)a * Q + i) * n + src];
+                st->fs[((long)a * Q + i) * n + c] = v;
                 r += v;
-                for (int d = 0; d < 3; ++d) jc[d] += CV[i][d] * v;
+                for (int d = 0; d < 3; ++d) jc[d] += L->cv[i][d] * v;
             }
             st->rho[a][c] = is_pressure(st, c) ? rho_held(st, c, a) : r;
         }
@@ -641,10 +687,10 @@ static void one_step(orc_state *st)
         for (int a = 0; a < 2; ++a) {
             double g[3] = {0, 0, 0};
             if (st->type[c] != SOLID) {
-                for (int i = 0; i < 19; ++i) {
-                    long m = neighbour(st, c, CV[i][0], CV[i][1], CV[i][2]);
+                for (int i = 0; i < Q; ++i) {
+                    long m = neighbour(st, c, L->cv[i][0], L->cv[i][1], L->cv[i][2]);
                     double v = rho_seen(st, m, 1 - a);
-                    for (int d = 0; d < 3; ++d) g[d] += weight(i) * v * CV[i][d] / CS2;
+                    for (int d = 0; d < 3; ++d) g[d] += L->w[i] * v * L->cv[i][d] / CS2;
                 }
             }
             for (int d = 0; d < 3; ++d) st->grad[a][d * n + c] = g[d];
@@ -698,11 +744,11 @@ static void one_step(orc_state *st)
             /* Atwood number of wetting vs non-wetting, its gradient and normal */
             double At_c = (r[w] - r[1 - w]) / (r[w] + r[1 - w]);
             double dAt[3] = {0, 0, 0};
-            for (int i = 0; i < 19; ++i) {
-                long m = neighbour(st, c, CV[i][0], CV[i][1], CV[i][2]);
+            for (int i = 0; i < Q; ++i) {
+                long m = neighbour(st, c, L->cv[i][0], L->cv[i][1], L->cv[i][2]);
                 double rw = rho_seen(st, m, w), rn = rho_seen(st, m, 1 - w);
                 double At = (rw + rn > 0.0) ? (rw - rn) / (rw + rn) : 0.0;
-                for (int d = 0; d < 3; ++d) dAt[d] += weight(i) * At * CV[i][d] / CS2;
+                for (int d = 0; d < 3; ++d) dAt[d] += L->w[i] * At * L->cv[i][d] / CS2;
             }
             double mag = sqrt(dAt[0] * dAt[0] + dAt[1] * dAt[1] + dAt[2] * dAt[2]);
             double H = (fabs(At_c) <= p->at_cut) ? 0.5 * mag : 0.0;
@@ -768,17 +814,17 @@ static void one_step(orc_state *st)
             /* reservoir: the rest equilibrium of the held densities */
             for (int a = 0; a < 2; ++a) {
                 double feq[19];
-                equilibrium(st->rho[a][c], uc, feq);
-                for (int i = 0; i < 19; ++i) st->f[((long)a * 19 + i) * n + c] = feq[i];
+                equilibrium(L, st->rho[a][c], uc, feq);
+                for (int i = 0; i < Q; ++i) st->f[((long)a * Q + i) * n + c] = feq[i];
             }
             continue;
         }
         for (int a = 0; a < 2; ++a) {
             double fin[19], fout[19], Fa[3];
-            for (int i = 0; i < 19; ++i) fin[i] = st->fs[((long)a * 19 + i) * n + c];
+            for (int i = 0; i < Q; ++i) fin[i] = st->fs[((long)a * Q + i) * n + c];
             for (int d = 0; d < 3; ++d) Fa[d] = st->F[a][d * n + c];
-            orc_collide_cell(fin, uc, Fa, p->tau[a], fout);
-            for (int i = 0; i < 19; ++i) st->f[((long)a * 19 + i) * n + c] = fout[i];
+            collide_cell(L, fin, uc, Fa, p->tau[a], fout);
+            for (int i = 0; i < Q; ++i) st->f[((long)a * Q + i) * n + c] = fout[i];
         }
     }
     st->steps += 1;

@@ -43,14 +43,14 @@ def rel_l2(a, b, mask=None):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def rest_only_populations(rhoA, rhoB):
+def rest_only_populations(rhoA, rhoB, Q=19):
     """Post-collision state whose streamed densities equal (rhoA, rhoB) exactly.
 
     All mass sits in the rest population, which streams onto itself, so the
     first step sees exactly these densities and zero momentum.
     """
     shape = np.shape(rhoA)
-    f = np.zeros((2, 19) + shape)
+    f = np.zeros((2, Q) + shape)
     f[0, 0] = rhoA
     f[1, 0] = rhoB
     return f

@@ -56,12 +56,13 @@ def test_collision_moments_match_bgk_with_force(tau):
 # --------------------------------------------------------------------------
 # Flow pins: shear-wave viscosity, Poiseuille, Darcy, Brinkman
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("lattice", ["d3q19", "d2q9"])
 @pytest.mark.parametrize("tau", [0.6, 1.0, 1.4])
-def test_shear_wave_decay_gives_lattice_viscosity(tau):
+def test_shear_wave_decay_gives_lattice_viscosity(tau, lattice):
     """u_x = U sin(k y) decays as exp(-nu k^2 t) with nu = (tau - 1/2)/3."""
     ny = 64
     shape = (1, ny, 1)
-    p = O.make_params(shape, tau=(tau, tau), wet=0)
+    p = O.make_params(shape, tau=(tau, tau), wet=0, lattice=lattice)
     cell = np.zeros(shape, np.uint8)
     k = 2 * np.pi / ny
     y = np.arange(ny)
@@ -104,6 +105,55 @@ def test_poiseuille_profile():
     nu = 1.0 / 6.0
     exact = g / (2 * nu) * (y - 0.5) * (W + 0.5 - y)
     assert np.max(np.abs(ux - exact)) / exact.max() < 1e-2
+
+
+def test_d2q9_is_the_plane_projection_of_d3q19_at_unit_tau():
+    """On a z-invariant state D3Q19 populations summed over c_z obey the D2Q9
+    step: the projected weights are 4/9, 1/9, 1/36, and equilibrium, force
+    term and every isotropic stencil project linearly.  At tau = 1 the
+    regularised part, whose projection would carry the zz moment, vanishes.
+    So the D2Q9 oracle and the D3Q19 oracle on one periodic plane agree to
+    round-off, with solid, gray (tensorial, capillary, residual switches),
+    Shan-Chen, walls and body forces (Eq. 4 is left out: its moment Hessian
+    has a zz entry on D3Q19)."""
+    rng = np.random.default_rng(8)
+    shape = (1, 12, 10)
+    cell = np.zeros(shape, np.uint8)
+    cell[rng.random(shape) < 0.1] = synth.SOLID
+    cell[(rng.random(shape) < 0.4) & (cell == 0)] = synth.GRAY
+    phi = np.where(cell == synth.GRAY, 0.15 + 0.4 * rng.random(shape), 1.0)
+    xx = np.arange(shape[2])[None, None, :] + np.zeros(shape)
+    ra = np.where(xx < 5, 1.0, 0.03) + 0.05 * rng.random(shape)
+    rb = 1.06 - ra
+    u0 = 0.01 * rng.standard_normal((3,) + shape)
+    u0[2] = 0.0
+    common = dict(G=1.1, tau=(1.0, 1.0), accel=((1e-4, 2e-5, 0), (0, -1e-4, 0)), rho_wall=(0.7, 0.2), wet=1)
+    curves = [O.make_curve(aniso=10.0)]
+    o3 = O.Oracle(O.make_params(shape, **common), cell, phi, curves=curves)
+    o2 = O.Oracle(O.make_params(shape, lattice="d2q9", **common), cell, phi, curves=curves)
+    # flipped residual flags, so that both hysteresis transitions occur
+    s = np.clip((rb / (ra + rb) - 0.03 / 1.03) / (1.0 / 1.03 - 0.03 / 1.03), 0, 1)
+    wet0 = np.where(cell == synth.GRAY, s < 0.5, s >= 0.5).astype(np.int32)
+    for o in (o3, o2):
+        o.init_fields(ra, rb, u0)
+        o.set_residual(np.zeros(shape), np.zeros(shape), wet0)
+    assert o2.Q == 9 and o3.Q == 19
+    vel19 = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1), (1, 1, 0),
+             (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1), (1, 0, -1), (-1, 0, 1), (0, 1, 1),
+             (0, -1, -1), (0, 1, -1), (0, -1, 1)]
+    vel9 = [(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (1, -1), (-1, 1)]
+    proj = np.zeros((9, 19))
+    for i, c in enumerate(vel19):
+        proj[vel9.index(c[:2]), i] = 1.0
+    for _ in range(25):
+        o3.step(1)
+        o2.step(1)
+    f3, f2 = o3.populations(), o2.populations()
+    np.testing.assert_allclose(np.einsum("qi,ai...->aq...", proj, f3), f2, rtol=0, atol=1e-13)
+    for x, y in zip(o3.fields(), o2.fields()):
+        np.testing.assert_allclose(x, y, rtol=0, atol=1e-13)
+    Rw, Ro, _ = o2.residual()
+    assert (Rw > 0).any() and (Ro > 0).any()
 
 
 def test_open_axis_equals_solid_rows():
@@ -241,7 +291,7 @@ def test_brinkman_channel():
 def _rest_state(p, cell, rhoA, rhoB, phi=None, curves=None):
     o = O.Oracle(p, cell, phi, curves=curves)
     o.init_fields(rhoA, rhoB)
-    o.set_populations(rest_only_populations(rhoA, rhoB))
+    o.set_populations(rest_only_populations(rhoA, rhoB, o.Q))
     o.step(1)
     return o
 
@@ -306,7 +356,8 @@ def test_capillary_force_flat_interface_telescopes():
         assert abs(total - (-0.02 * scale * jump)) < tol * 0.02 * scale
 
 
-def test_csf_force_on_cylinder_matches_continuum():
+@pytest.mark.parametrize("lattice", ["d3q19", "d2q9"])
+def test_csf_force_on_cylinder_matches_continuum(lattice):
     """Eq. 4 on a smooth cylindrical interface: div n = 1/r in two dimensions.
 
     phi^A = rho^B = b0 + b1 tanh((r - R)/w) rises outward, so n^A = r-hat and
@@ -322,7 +373,8 @@ def test_csf_force_on_cylinder_matches_continuum():
     rhoB = (b0 + b1 * np.tanh((r - R) / w))[None]
     rhoA = (0.6 - 0.2 * np.tanh((r - R) / w))[None]
     kappa = -0.045
-    p = O.make_params(shape, kappa=kappa, csf_everywhere=1, phi_avg=(0.515, 0.515), phi_max=(1.0, 1.0))
+    p = O.make_params(shape, kappa=kappa, csf_everywhere=1, phi_avg=(0.515, 0.515), phi_max=(1.0, 1.0),
+                      lattice=lattice)
     o = _rest_state(p, np.zeros(shape, np.uint8), rhoA, rhoB)
     F = o.force_term(O.TERM_CSF, 0)[:2, 0]
     rh = np.stack([(x - cx) / r, (y - cy) / r])
@@ -382,7 +434,8 @@ def test_mass_conserved_with_walls_and_gray_cells():
 # --------------------------------------------------------------------------
 # Laplace's law (2-D droplets, Sec. III.A)
 # --------------------------------------------------------------------------
-def test_laplace_law_two_dimensional():
+@pytest.mark.parametrize("lattice", ["d3q19", "d2q9"])
+def test_laplace_law_two_dimensional(lattice):
     """Delta p = sigma / R (Sec. III.A): Delta p * R is nearly the same for every R.
 
     R is the mass-equivalent radius of the droplet.  Diffuse-interface
@@ -396,7 +449,7 @@ def test_laplace_law_two_dimensional():
     dps, radii = [], []
     for R in (10.0, 14.0, 18.0):
         rA, rB = synth.cylinder_droplet_fields(shape, R, (32, 32), 1.0, 0.03)
-        o = O.Oracle(O.make_params(shape, G=1.1), np.zeros(shape, np.uint8))
+        o = O.Oracle(O.make_params(shape, G=1.1, lattice=lattice), np.zeros(shape, np.uint8))
         o.init_fields(rA, rB)
         o.step(3000)
         a = o.fields()[0]
