@@ -70,6 +70,12 @@ enum lbm_status {
 
 enum lbm_mem { LBM_MEM_HOST = 0, LBM_MEM_DEVICE = 1 };
 
+/* Velocity set.  D3Q19 (default) is the method's lattice.  D2Q9 runs the same
+ * step on one plane (nz = 1; the paper's two-dimensional experiments of
+ * Sec. III) with weights 4/9, 1/9, 1/36: F32 storage only, two launches per
+ * step, not in batches or the adjoint (LBM_ERR_ARG there). */
+enum lbm_lattice { LBM_LATTICE_D3Q19 = 0, LBM_LATTICE_D2Q9 = 1 };
+
 enum lbm_cell {
     LBM_CELL_PORE = 0,
     LBM_CELL_SOLID = 1,
@@ -121,6 +127,7 @@ typedef struct lbm_params {
     double probe_center[3]; /* pressure probe for lbm_obs.dp */
     double probe_r_in;      /* inside: distance < probe_r_in */
     double probe_r_out;     /* outside: distance > probe_r_out */
+    int lattice;            /* enum lbm_lattice */
 } lbm_params;
 
 /* Constitutive curves of one pore type (Appendix: Kozeny-Carman K0,

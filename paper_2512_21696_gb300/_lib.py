@@ -24,6 +24,7 @@ LBM_MEM_HOST = 0
 LBM_MEM_DEVICE = 1
 
 LBM_CELL_PORE, LBM_CELL_SOLID, LBM_CELL_GRAY, LBM_CELL_INLET, LBM_CELL_OUTLET = 0, 1, 2, 3, 4
+LBM_LATTICE_D3Q19, LBM_LATTICE_D2Q9 = 0, 1
 LBM_STORAGE_F32, LBM_STORAGE_F16S, LBM_STORAGE_BF16S = 0, 1, 2
 LBM_MAX_PORE_TYPES = 16
 
@@ -52,6 +53,7 @@ class lbm_params(C.Structure):
         ("probe_center", C.c_double * 3),
         ("probe_r_in", C.c_double),
         ("probe_r_out", C.c_double),
+        ("lattice", C.c_int),
     ]
 
 

@@ -41,6 +41,7 @@ bool valid_curve(const lbm_constitutive &c)
 size_t pop_bytes(const lbm_ctx *ctx)
 {
     const size_t n = (size_t)ctx->n;
+    if (ctx->p.lattice == LBM_LATTICE_D2Q9) return 2 * 9 * n * sizeof(float);
     switch (ctx->p.storage) {
     case LBM_STORAGE_F32: return 2 * lbm::Q * n * sizeof(float);
     case LBM_STORAGE_F16R:
@@ -57,6 +58,7 @@ void fill_device_params(lbm_ctx *ctx)
     d.ny = p.ny;
     d.nz = p.nz;
     for (int k = 0; k < 3; ++k) d.per[k] = p.periodic[k] ? 1 : 0;
+    if (p.lattice == LBM_LATTICE_D2Q9) d.per[2] = 1;  // one plane: z-invariant stencils of the geometry pass
     d.n = ctx->n;
     for (int a = 0; a < 2; ++a) {
         d.omega_fac[a] = (float)(1.0 - 1.0 / p.tau[a]);
@@ -135,6 +137,8 @@ int validate_params(const lbm_params *p)
     if (!(p->s_lo >= 0 && p->s_lo < p->s_hi && p->s_hi <= 1)) return LBM_ERR_ARG;
     if (!(p->eps_n > 0 && p->kr_min > 0 && p->at_cut >= 0 && p->c_g >= 0)) return LBM_ERR_ARG;
     if (p->storage < LBM_STORAGE_F32 || p->storage > LBM_STORAGE_BF16R) return LBM_ERR_ARG;
+    if (p->lattice != LBM_LATTICE_D3Q19 && p->lattice != LBM_LATTICE_D2Q9) return LBM_ERR_ARG;
+    if (p->lattice == LBM_LATTICE_D2Q9 && (p->nz != 1 || p->storage != LBM_STORAGE_F32)) return LBM_ERR_ARG;
     for (int a = 0; a < 2; ++a)
         for (int k = 0; k < 3; ++k)
             if (!std::isfinite(p->body_accel[a][k])) return LBM_ERR_ARG;
@@ -229,6 +233,7 @@ int lbm_default_params(lbm_params *p, int nx, int ny, int nz)
     p->probe_center[2] = 0.5 * (nz - 1);
     p->probe_r_in = 0.0;
     p->probe_r_out = INFINITY;
+    p->lattice = LBM_LATTICE_D3Q19;
     return LBM_OK;
 }
 
@@ -435,7 +440,10 @@ int lbm_init_fields(lbm_ctx *ctx, const float *rhoA, const float *rhoB, const fl
     if ((rc = stage_in(rhoB, N * sizeof(float), mem, ctx->stream, sb, &db)) != LBM_OK) return rc;
     if (u && (rc = stage_in(u, 3 * N * sizeof(float), mem, ctx->stream, su, &du)) != LBM_OK) return rc;
     ctx->cur = 0;
-    LBM_CUDA(lbm::launch_init(ctx, (const float *)da, (const float *)db, (const float *)du));
+    if (ctx->p.lattice == LBM_LATTICE_D2Q9)
+        LBM_CUDA(lbm::launch_d2q9_init(ctx, (const float *)da, (const float *)db, (const float *)du));
+    else
+        LBM_CUDA(lbm::launch_init(ctx, (const float *)da, (const float *)db, (const float *)du));
     if (mem == LBM_MEM_HOST) LBM_CUDA(cudaStreamSynchronize(ctx->stream));
     ctx->steps = 0;
     ctx->has_fields = true;
@@ -449,7 +457,9 @@ int lbm_step(lbm_ctx *ctx, int nsteps)
     DeviceGuard g(ctx->dev);
     if (!g.ok) return LBM_ERR_CUDA;
     for (int k = 0; k < nsteps; ++k) {
-        if (ctx->p.storage == LBM_STORAGE_F16S || ctx->p.storage == LBM_STORAGE_BF16S) {
+        if (ctx->p.lattice == LBM_LATTICE_D2Q9) {
+            LBM_CUDA(lbm::launch_d2q9_step(ctx, k == nsteps - 1));
+        } else if (ctx->p.storage == LBM_STORAGE_F16S || ctx->p.storage == LBM_STORAGE_BF16S) {
             LBM_CUDA(lbm::launch_fused_lp(ctx, k == nsteps - 1));
         } else if (ctx->path == 1 && ctx->p.storage == LBM_STORAGE_F32) {
             LBM_CUDA(lbm::launch_density(ctx));

@@ -343,6 +343,8 @@ int lbm_batch_create(lbm_batch **out, int nruns, const lbm_params *runs)
         if (!same_physics(runs[0], runs[r])) return LBM_ERR_ARG;
     }
     if (runs[0].storage == LBM_STORAGE_F16S || runs[0].storage == LBM_STORAGE_BF16S) return LBM_ERR_ARG;
+    for (int r = 0; r < nruns; ++r)
+        if (runs[r].lattice != LBM_LATTICE_D3Q19) return LBM_ERR_ARG;
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_ERR_OOM;
     b->p0 = runs[0];

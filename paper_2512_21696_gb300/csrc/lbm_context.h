@@ -66,6 +66,8 @@ cudaError_t launch_density(lbm_ctx *ctx);
 cudaError_t launch_collide(lbm_ctx *ctx, bool write_macro);
 cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro);
 cudaError_t launch_fused_lp(lbm_ctx *ctx, bool write_macro);
+cudaError_t launch_d2q9_init(lbm_ctx *ctx, const float *rhoA, const float *rhoB, const float *u);
+cudaError_t launch_d2q9_step(lbm_ctx *ctx, bool write_macro);
 cudaError_t launch_geometry(lbm_ctx *ctx, const uint8_t *ptype);
 cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16);
 cudaError_t launch_static_out(lbm_ctx *ctx, float *kinv6, float *pcs, float *swirr, float *sores);

@@ -14,7 +14,7 @@ from paper_2512_21696_gb300 import synth
 DEFAULTS = dict(G=0.0, kappa=0.0, tau=(1.0, 1.0), accel=((0, 0, 0), (0, 0, 0)), csf_everywhere=0,
                 rho_wall=(0.515, 0.515), wet=1, rho_hi=1.0, rho_lo=0.03, periodic=(1, 1, 1),
                 s_lo=0.1, s_hi=0.9, at_cut=0.95, kr_min=1e-6, c_g=1.0, phi_avg=(0.515, 0.515),
-                phi_max=(1.0, 1.0), held=None)
+                phi_max=(1.0, 1.0), held=None, lattice="d3q19")
 CURVE = dict(kc_d=1.0, pd=0.02, lam=2.0, swr=0.15, nw=3.0, nn=2.0, phi_ref=0.35, f_max=3.5,
              f_min=0.575, aniso=1.0, thomeer_g=0.0)
 
@@ -59,6 +59,7 @@ def gpu_params(case: Case, **extra):
     p.rho_hi, p.rho_lo = s["rho_hi"], s["rho_lo"]
     p.s_lo, p.s_hi, p.at_cut = s["s_lo"], s["s_hi"], s["at_cut"]
     p.eps_n, p.kr_min, p.c_g = s["eps_n"], s["kr_min"], s["c_g"]
+    p.lattice = {"d3q19": 0, "d2q9": 1}[s["lattice"]]
     cx, cy, cz, rin, rout = case.probe
     p.probe_center[0], p.probe_center[1], p.probe_center[2] = cx, cy, cz
     p.probe_r_in, p.probe_r_out = rin, min(rout, 1e300)
@@ -74,7 +75,7 @@ def oracle_params(case: Case):
                          phi_avg=s["phi_avg"], phi_max=s["phi_max"], csf_everywhere=s["csf_everywhere"],
                          rho_wall=s["rho_wall"], accel=s["accel"], wet=s["wet"], rho_hi=s["rho_hi"],
                          rho_lo=s["rho_lo"], s_lo=s["s_lo"], s_hi=s["s_hi"], at_cut=s["at_cut"],
-                         eps_n=s["eps_n"], kr_min=s["kr_min"], c_g=s["c_g"])
+                         eps_n=s["eps_n"], kr_min=s["kr_min"], c_g=s["c_g"], lattice=s["lattice"])
 
 
 def run_gpu(case: Case, steps: int, device_arrays=False, path=0, tile=0, **extra):
@@ -199,6 +200,55 @@ def imbibition(n=32, seed=synth.SEED_BASE + 6, dp=0.02, tau=(1.0, 1.0), nz=None)
     held = ((f32(0.03), f32(1.0 + dp)), (f32(1.0), f32(0.03)))
     return Case(f"imbibition{cell.shape}", cell.shape, cell, phi, rA, rB, ptype=ptype, G=1.1, kappa=-0.045,
                 tau=tau, rho_wall=(0.03, 1.0), wet=1, periodic=(1, 1, 0), held=held)
+
+
+def droplet2d(n=100, R=40, kappa=0.0, csf_everywhere=1, tau=(1.0, 1.0), G=1.1):
+    """Sec. III.A on D2Q9: a droplet of A (radius R) in B on an n^2 periodic
+    plane, rho 1.0 / 0.03."""
+    shape = (1, n, n)
+    c = n // 2
+    rA, rB = synth.cylinder_droplet_fields(shape, R, (c, c), 1.0, 0.03)
+    return Case(f"droplet2d{n}_R{R}", shape, np.zeros(shape, np.uint8), np.ones(shape), rA, rB, G=G, kappa=kappa,
+                csf_everywhere=csf_everywhere, tau=tau, lattice="d2q9", probe=(c, c, 0, R - 4, R + 4))
+
+
+def mixed2d(shape=(1, 13, 17), seed=9, periodic=(1, 1, 1), tau=(0.8, 1.3), thomeer=0.35):
+    """D2Q9 counterpart of mixed_features: solid, gray (two pore types, one on
+    a Thomeer curve, tensorial), wetting walls, CSF in gray cells, body
+    forces, both residual transitions, open or periodic axes."""
+    rng = np.random.default_rng(seed)
+    cell = np.zeros(shape, np.uint8)
+    cell[rng.random(shape) < 0.12] = synth.SOLID
+    cell[(rng.random(shape) < 0.35) & (cell == 0)] = synth.GRAY
+    phi = np.where(cell == synth.GRAY, 0.15 + 0.4 * rng.random(shape), 1.0)
+    yy, xx = np.meshgrid(np.arange(shape[1]), np.arange(shape[2]), indexing="ij")
+    blocks = (((xx // 4 + yy // 4) % 2) == 0)[None]
+    ra = np.where(blocks, 1.0, 0.03) + 0.05 * rng.random(shape)
+    rb = 1.06 - ra
+    u0 = 0.01 * rng.standard_normal((3,) + shape)
+    u0[2] = 0.0
+    ptype = (rng.random(shape) < 0.5).astype(np.uint8)
+    curves = [dict(CURVE, aniso=10.0), dict(CURVE, kc_d=1.5, pd=0.03, lam=1.5, swr=0.1, nw=2.5, nn=1.5, aniso=3.0,
+                                           thomeer_g=thomeer)]
+    return Case(f"mixed2d{shape}", shape, cell, phi, ra, rb, u=u0, ptype=ptype, curves=curves, G=1.1,
+                kappa=-0.045, tau=tau, accel=((1e-4, 2e-5, 0), (0, -1e-4, 0)), rho_wall=(0.7, 0.2), wet=1,
+                periodic=periodic, lattice="d2q9")
+
+
+def imbibition2d(nx=64, ny=96, seed=synth.SEED_BASE + 9, dp=0.02):
+    """The pressure-driven imbibition set-up on D2Q9: a plane of the
+    multiscale-rock recipe between a wetting-B inlet row (y = 0) and a
+    non-wetting-A outlet row (y = ny - 1), y not periodic."""
+    cell3, phi3, ptype3 = synth.drainage_geometry(max(nx, ny), seed)
+    cell, phi, ptype = cell3[:1, :ny, :nx].copy(), phi3[:1, :ny, :nx], ptype3[:1, :ny, :nx]
+    cell[:, 0, :], cell[:, -1, :] = synth.INLET, synth.OUTLET
+    yy = np.arange(ny)[None, :, None] + np.zeros(cell.shape, np.int64)
+    wet = yy < 4
+    rA, rB = np.where(wet, 0.03, 1.0), np.where(wet, 1.0, 0.03)
+    f32 = lambda v: float(np.float32(v))
+    held = ((f32(0.03), f32(1.0 + dp)), (f32(1.0), f32(0.03)))
+    return Case(f"imbibition2d{cell.shape}", cell.shape, cell, phi, rA, rB, ptype=ptype, G=1.1, kappa=-0.045,
+                rho_wall=(0.03, 1.0), wet=1, periodic=(1, 0, 1), held=held, lattice="d2q9")
 
 
 def adjoint_case(n=8, seed=21, shape=None, steps_hint=None, thomeer=0.0):

@@ -65,6 +65,12 @@ def test_create_rejects_bad_parameters_before_touching_a_device():
     bad = lbm.lbm_default_params(4, 4, 4, storage=7)
     with pytest.raises(lbm.LbmError):
         lbm.lbm_create(bad)
+    # D2Q9 runs one plane with F32 storage; unknown lattices are refused
+    for kw in (dict(nz=2, lattice=1), dict(nz=1, lattice=1, storage=3), dict(nz=1, lattice=2)):
+        nz = kw.pop("nz")
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_create(lbm.lbm_default_params(4, 4, nz, **kw))
+        assert e.value.code == -1
 
 
 def test_null_handles_are_rejected():
