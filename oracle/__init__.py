@@ -45,6 +45,7 @@ class OrcParams(C.Structure):
         ("eps_n", C.c_double), ("kr_min", C.c_double), ("c_g", C.c_double),
         ("rho_in", C.c_double * 2), ("rho_out", C.c_double * 2),
         ("lattice", C.c_int),
+        ("mss", C.c_double),
     ]
 
 
@@ -86,6 +87,7 @@ def _load():
         lib.orc_observables.argtypes = [P, dp, dp]
         lib.orc_set_populations.argtypes = [P, dp]
         lib.orc_set_pressure.argtypes = [P, dp, dp]
+        lib.orc_set_mss.argtypes = [P, C.c_double]
         lib.orc_get_populations.argtypes = [P, dp]
         lib.orc_set_residual.argtypes = [P, dp, dp, ip]
         lib.orc_get_residual.argtypes = [P, dp, dp, ip]
@@ -151,6 +153,7 @@ def make_params(shape, **kw) -> OrcParams:
     p.kr_min = kw.pop("kr_min", 1e-6)
     p.c_g = kw.pop("c_g", 1.0)
     p.lattice = {"d3q19": 0, "d2q9": 1}[kw.pop("lattice", "d3q19")]
+    p.mss = kw.pop("mss", 0.0)
     rin = kw.pop("rho_in", (rho_hi, rho_lo))
     rout = kw.pop("rho_out", (rho_hi, rho_lo))
     for a in range(2):
@@ -247,6 +250,10 @@ class Oracle:
         return dict(mass=(out[0], out[1]), sat=out[2], flux_out=out[3],
                     flux_vol=(out[4], out[5], out[6]), max_u=out[7], dp=out[8],
                     nan_count=int(out[9]))
+
+    def set_mss(self, rate):
+        """Mass-sink-source rate (wetting gains m I per step) from the next step."""
+        self.lib.orc_set_mss(self._h, float(rate))
 
     def set_pressure(self, rho_in, rho_out):
         """Densities (A, B) held in the inlet and outlet cells from the next step."""

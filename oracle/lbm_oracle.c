@@ -54,6 +54,15 @@
  *     streams into the domain.  The pressure of a reservoir is
  *     p = cs^2 (rhoA + rhoB) + G rhoA rhoB.
  *
+ *   - Mass-sink-source (the Appendix's relative-permeability runs move the
+ *     saturation between stages by injecting water near the oil-water
+ *     interface; its definition is in the paper's refs. [12, 15]).  Reading:
+ *     in every fluid cell that is not a reservoir, the collision adds the
+ *     rest equilibrium w_i dm to the wetting component and w_i (-dm) to the
+ *     other, dm = m I, with m the run's rate (lattice density per step) and
+ *     I = max(0, (4 r_w r_n - I_b) / (1 - I_b)), r = rho^a / (rho^w + rho^n),
+ *     I_b = 4 r_lo r_hi the value in either bulk: zero in the bulks, one in
+ *     the middle of an interface.  Cell mass and momentum are unchanged.
  *   - D2Q9: the same step on one plane with the nine-velocity set (weights
  *     4/9, 1/9, 1/36, cs^2 = 1/3); every formula above is written for
  *     three-component vectors whose z parts vanish, and the identity in the
@@ -92,6 +101,7 @@ typedef struct {
     double s_lo, s_hi, at_cut, eps_n, kr_min, c_g;
     double rho_in[2], rho_out[2]; /* densities held in inlet / outlet cells */
     int lattice;                  /* 0: D3Q19; 1: D2Q9 (nz = 1) */
+    double mss;                   /* mass-sink-source rate m (0: off) */
 } orc_params;
 
 typedef struct {
@@ -601,6 +611,9 @@ void orc_init_fields(orc_state *st, const double *rhoA, const double *rhoB, cons
     st->steps = 0;
 }
 
+/* New mass-sink-source rate, used from the next step on. */
+void orc_set_mss(orc_state *st, double rate) { st->p.mss = rate; }
+
 /* New reservoir densities, used from the next step on. */
 void orc_set_pressure(orc_state *st, const double rho_in[2], const double rho_out[2])
 {
@@ -819,12 +832,23 @@ static void one_step(orc_state *st)
             }
             continue;
         }
+        /* mass-sink-source: dm = m I moved from the non-wetting to the wetting component */
+        double dm = 0.0;
+        if (p->mss != 0.0) {
+            double rt = st->rho[0][c] + st->rho[1][c];
+            double rw = st->rho[w][c] / rt, rn = st->rho[1 - w][c] / rt;
+            double rlo = p->rho_lo / (p->rho_hi + p->rho_lo), rhi = p->rho_hi / (p->rho_hi + p->rho_lo);
+            double Ib = 4.0 * rlo * rhi;
+            double I = (4.0 * rw * rn - Ib) / (1.0 - Ib);
+            dm = p->mss * (I > 0.0 ? I : 0.0);
+        }
         for (int a = 0; a < 2; ++a) {
             double fin[19], fout[19], Fa[3];
             for (int i = 0; i < Q; ++i) fin[i] = st->fs[((long)a * Q + i) * n + c];
             for (int d = 0; d < 3; ++d) Fa[d] = st->F[a][d * n + c];
             collide_cell(L, fin, uc, Fa, p->tau[a], fout);
-            for (int i = 0; i < Q; ++i) st->f[((long)a * Q + i) * n + c] = fout[i];
+            double sgn = a == w ? 1.0 : -1.0;
+            for (int i = 0; i < Q; ++i) st->f[((long)a * Q + i) * n + c] = fout[i] + sgn * L->w[i] * dm;
         }
     }
     st->steps += 1;

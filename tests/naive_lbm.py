@@ -275,6 +275,15 @@ class NaiveLBM:
                 terms[a][k] = np.where(self.pres[None], 0.0, terms[a][k])
             F.append(sum(terms[a].values()))
         fnew = np.stack([collide(fs[a], u, F[a], p["tau"][a]) for a in range(2)])
+        if p.get("mss", 0.0):
+            # mass-sink-source: rest equilibrium of +dm (wetting) and -dm (other)
+            rw, rn = rho[w] / rt, rho[1 - w] / rt
+            r_lo = p["rho_lo"] / (p["rho_hi"] + p["rho_lo"])
+            ib = 4 * r_lo * (1 - r_lo)
+            dm = p["mss"] * np.maximum((4 * rw * rn - ib) / (1 - ib), 0.0)
+            dm = np.where(self.solid | self.pres, 0.0, dm)
+            fnew[w] = fnew[w] + WGT[:, None, None, None] * dm[None]
+            fnew[1 - w] = fnew[1 - w] - WGT[:, None, None, None] * dm[None]
         rest = np.zeros((3,) + self.cell.shape, dt)
         fnew = np.where(self.pres[None, None], np.stack([equilibrium(rho[a], rest) for a in range(2)]), fnew)
         self.f = np.where(self.solid[None, None], 0.0, fnew).astype(dt)

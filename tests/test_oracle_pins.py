@@ -566,6 +566,35 @@ def test_thomeer_residual_crossings(g):
     assert np.all(st2["swirr"] >= st["swirr"]) and np.any(st2["swirr"] > st["swirr"])
 
 
+@pytest.mark.parametrize("lattice", ["d3q19", "d2q9"])
+def test_mass_sink_source_special_cases(lattice):
+    """The mass-sink-source term moves mass from the non-wetting to the
+    wetting component in rest equilibrium: from a uniform 50/50 mixture at
+    rest (the middle of an interface, indicator 1) one step moves exactly m
+    per cell, the total and the momentum stay unchanged; from the bulk state
+    (rho_hi, rho_lo) (indicator 0) nothing moves."""
+    shape = (1, 6, 7) if lattice == "d2q9" else (5, 6, 7)
+    n = int(np.prod(shape))
+    m = 3e-3
+    for (rw, rn), moved in (((0.515, 0.515), m), ((1.0, 0.03), 0.0)):
+        out = []
+        for rate in (0.0, m):
+            o = O.Oracle(O.make_params(shape, G=1.1, wet=1, mss=rate, lattice=lattice), np.zeros(shape, np.uint8))
+            o.init_fields(np.full(shape, rn), np.full(shape, rw))
+            o.step(1)
+            out.append((o.observables(), o.populations()))
+        (ob0, f0), (ob1, f1) = out
+        # the post-collision populations carry it (the fields of the step do not yet)
+        mass0, mass1 = f0.reshape(2, -1).sum(axis=1), f1.reshape(2, -1).sum(axis=1)
+        assert abs((mass1[1] - mass0[1]) - n * moved) < 1e-12 * n
+        assert abs((mass1[0] - mass0[0]) + n * moved) < 1e-12 * n
+        # the added populations are the rest equilibrium: no momentum
+        df = f1 - f0
+        assert np.allclose(df.sum(axis=1)[1], moved, atol=1e-14) and np.allclose(df.sum(axis=1)[0], -moved, atol=1e-14)
+        # every opposite pair gains the same amount (i odd and i + 1 are opposites in both sets)
+        assert np.abs(df[:, 1::2] - df[:, 2::2]).max() < 1e-15
+
+
 def test_residual_hysteresis_switches():
     """Wet cells with s < s_lo take residual water; dry cells with s > s_hi take residual oil."""
     n = 8
@@ -597,7 +626,7 @@ def test_residual_hysteresis_switches():
 # --------------------------------------------------------------------------
 # Brute force: the C oracle against the independent NumPy evaluator
 # --------------------------------------------------------------------------
-def _bruteforce_case(seed, csf_everywhere, tau, pressure=False, thomeer=0.0):
+def _bruteforce_case(seed, csf_everywhere, tau, pressure=False, thomeer=0.0, mss=0.0):
     rng = np.random.default_rng(seed)
     n = 8
     shape = (n, n, n)
@@ -617,7 +646,7 @@ def _bruteforce_case(seed, csf_everywhere, tau, pressure=False, thomeer=0.0):
     rb = 1.06 - ra
     u0 = 0.01 * rng.standard_normal((3,) + shape)
     common = dict(G=1.1, kappa=-0.045, tau=tau, accel=((1e-4, 2e-5, 0), (0, -1e-4, 3e-5)),
-                  c_g=1.0, rho_wall=(0.7, 0.2), wet=1, csf_everywhere=csf_everywhere, **bc)
+                  c_g=1.0, rho_wall=(0.7, 0.2), wet=1, csf_everywhere=csf_everywhere, mss=mss, **bc)
     curve = dict(kc_d=1.0, pd=0.02, swr=0.15, nw=3.0, nn=2.0, phi_ref=0.35, f_max=3.5,
                  f_min=0.575, aniso=10.0, thomeer_g=thomeer)
     o = O.Oracle(O.make_params(shape, **common), cell, phi, curves=[O.make_curve(lam=2.0, **curve)])
@@ -634,12 +663,13 @@ def _bruteforce_case(seed, csf_everywhere, tau, pressure=False, thomeer=0.0):
     return o, nv, cell
 
 
-@pytest.mark.parametrize("csf_everywhere,tau,pressure,thomeer", [(0, (0.8, 1.3), False, 0.0),
-                                                                 (1, (1.0, 1.0), False, 0.0),
-                                                                 (0, (0.8, 1.3), True, 0.0),
-                                                                 (0, (0.8, 1.3), False, 0.35)])
-def test_bruteforce_against_numpy_evaluator(csf_everywhere, tau, pressure, thomeer):
-    o, nv, cell = _bruteforce_case(5, csf_everywhere, tau, pressure, thomeer)
+@pytest.mark.parametrize("csf_everywhere,tau,pressure,thomeer,mss", [(0, (0.8, 1.3), False, 0.0, 0.0),
+                                                                     (1, (1.0, 1.0), False, 0.0, 0.0),
+                                                                     (0, (0.8, 1.3), True, 0.0, 0.0),
+                                                                     (0, (0.8, 1.3), False, 0.35, 0.0),
+                                                                     (0, (0.8, 1.3), True, 0.0, 2e-3)])
+def test_bruteforce_against_numpy_evaluator(csf_everywhere, tau, pressure, thomeer, mss):
+    o, nv, cell = _bruteforce_case(5, csf_everywhere, tau, pressure, thomeer, mss)
     st = o.static()
     np.testing.assert_allclose(np.moveaxis(st["kinv"], (0, 1), (-2, -1)), nv.geo["kinv"],
                                rtol=1e-12, atol=0)
