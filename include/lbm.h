@@ -251,6 +251,32 @@ LBM_API int lbm_step(lbm_ctx *ctx, int nsteps);
  * LBM_ERR_ARG on a NULL pointer or invalid densities.  No device work. */
 LBM_API int lbm_set_pressure(lbm_ctx *ctx, const double rho_in[2], const double rho_out[2]);
 
+/* Mass-sink-source (the Appendix's relative-permeability runs inject water
+ * around the oil-water interface to move between saturation stages; the
+ * paper defines it in its refs. [12, 15]).  Reading: in every fluid cell that
+ * is not a reservoir, each step's collision moves dm = rate * I from the
+ * non-wetting to the wetting component as rest equilibrium (w_i dm per
+ * population; cell mass and momentum unchanged), with the interface
+ * indicator I = max(0, (4 r_w r_n - I_b) / (1 - I_b)), r = rho^a / rho,
+ * I_b = 4 r_lo r_hi its value in either bulk (r_lo = rho_lo/(rho_hi +
+ * rho_lo)): zero in the bulks, one in the middle of an interface.
+ * rate (lattice density per step; negative drains water) takes effect from
+ * the next step; 0 switches the term off (and the plain march runs again).
+ * Works on a run of a batch.  LBM_ERR_ARG for a non-finite rate.  No device
+ * work. */
+LBM_API int lbm_set_mss(lbm_ctx *ctx, double rate);
+
+/* Saturation controller around the mass-sink-source: every check_every
+ * steps the rate is set to clamp(gain (target - S), -max_rate, max_rate)
+ * (0 within tol), S = lbm_obs.sat, until S is within tol of the target at a
+ * check or max_steps steps ran; the rate is 0 on return.  *steps_done
+ * receives the steps taken.  LBM_OK when the target was reached,
+ * LBM_ERR_TIMEOUT otherwise, LBM_ERR_ARG on invalid arguments (target in
+ * [0, 1], gain > 0, max_rate > 0, tol > 0, check_every >= 1, max_steps >= 1).
+ * Synchronous. */
+LBM_API int lbm_mss_to_saturation(lbm_ctx *ctx, double target, double gain, double max_rate, double tol,
+                                  int check_every, int max_steps, int *steps_done);
+
 /* Stepped-pressure protocol of the imbibition set-ups (Sec. I: the pressure
  * difference between the two boundaries is lowered level by level and a
  * steady state is recorded at each level; the Appendix evaluates Pc(Sw) the
@@ -376,6 +402,13 @@ LBM_API int lbm_batch_tune(lbm_batch *b, int trial_steps, int *tiles_out);
 LBM_API int lbm_batch_info(lbm_batch *b, long long *cells, long long *steps, long long *launches, int *ngroups);
 LBM_API int lbm_batch_observables(lbm_batch *b, lbm_obs *out);
 LBM_API int lbm_batch_step_to_steady(lbm_batch *b, int check_every, double rel_tol, int max_steps, int *steps_done);
+
+/* lbm_mss_to_saturation for every run of a batch at once, targets[nruns]
+ * (host array): each run has its own rate; the batch steps until every run
+ * is within tol of its target at a check (LBM_OK) or max_steps ran
+ * (LBM_ERR_TIMEOUT).  All rates are 0 on return.  Synchronous. */
+LBM_API int lbm_batch_mss_to_saturation(lbm_batch *b, const double *targets, double gain, double max_rate,
+                                        double tol, int check_every, int max_steps, int *steps_done);
 
 /* Number of kernels the context has launched since creation. */
 LBM_API int lbm_launch_count(lbm_ctx *ctx, long long *count);

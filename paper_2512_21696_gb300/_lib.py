@@ -91,7 +91,7 @@ EXPORTS = [
     "lbm_profile_read", "lbm_launch_count", "lbm_struct_size", "lbm_observables_noalloc", "lbm_set_kernel",
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_run", "lbm_batch_step", "lbm_batch_tune", "lbm_batch_info",
     "lbm_adjoint_run", "lbm_batch_observables", "lbm_batch_step_to_steady", "lbm_set_pressure",
-    "lbm_pressure_levels",
+    "lbm_pressure_levels", "lbm_set_mss", "lbm_mss_to_saturation", "lbm_batch_mss_to_saturation",
 ]
 
 _lock = threading.Lock()
@@ -140,6 +140,11 @@ def load(build_if_needed: bool = True):
                                                 C.POINTER(C.c_double), vp, C.POINTER(lbm_obs)]
         lib.lbm_set_kernel.argtypes = [P, C.c_int, C.c_int]
         lib.lbm_set_pressure.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.lbm_set_mss.argtypes = [P, C.c_double]
+        lib.lbm_mss_to_saturation.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
+                                              C.POINTER(C.c_int)]
+        lib.lbm_batch_mss_to_saturation.argtypes = [P, C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double,
+                                                    C.c_int, C.c_int, C.POINTER(C.c_int)]
         lib.lbm_pressure_levels.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
                                             C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
         lib.lbm_adjoint_run.argtypes = [P, C.POINTER(lbm_loss), C.c_int, C.c_int, vp, C.c_int,

@@ -716,7 +716,8 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
     if (!ctx || !L || nsteps < 1 || ckpt < 1 || !dL_dphi) return LBM_ERR_ARG;
     if (mem != LBM_MEM_HOST && mem != LBM_MEM_DEVICE) return LBM_ERR_ARG;
     if (!(L->q_target != 0.0) || !std::isfinite(L->q_target) || !std::isfinite(L->s_target)) return LBM_ERR_ARG;
-    if (ctx->p.storage != LBM_STORAGE_F32 || ctx->view || ctx->n_held > 0 || ctx->p.lattice != LBM_LATTICE_D3Q19)
+    if (ctx->p.storage != LBM_STORAGE_F32 || ctx->view || ctx->n_held > 0 || ctx->p.lattice != LBM_LATTICE_D3Q19 ||
+        ctx->mss != 0.0)
         return LBM_ERR_ARG;
     if (!ctx->has_fields) return LBM_ERR_STATE;
     DeviceGuard dg(ctx->dev);

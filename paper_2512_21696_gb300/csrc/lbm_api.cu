@@ -87,6 +87,9 @@ void fill_device_params(lbm_ctx *ctx)
             d.held[side][a][0] = (float)v;
             d.held[side][a][1] = (float)(v - (double)(float)v);
         }
+    d.mss = (float)ctx->mss;
+    d.mss_ib = (float)(4.0 * r_lo * r_hi);
+    d.mss_inv = (float)(1.0 / (1.0 - 4.0 * r_lo * r_hi));
     d.storage = p.storage;
     {
         const double ww = p.rho_wall[p.wet_idx], wn = p.rho_wall[1 - p.wet_idx];
@@ -388,6 +391,43 @@ int lbm_set_pressure(lbm_ctx *ctx, const double rho_in[2], const double rho_out[
     fill_device_params(ctx);
     if (ctx->owner) lbm::batch_runs_changed(ctx->owner);
     return LBM_OK;
+}
+
+int lbm_set_mss(lbm_ctx *ctx, double rate)
+{
+    if (!ctx || !std::isfinite(rate)) return LBM_ERR_ARG;
+    ctx->mss = rate;
+    fill_device_params(ctx);
+    if (ctx->owner) lbm::batch_runs_changed(ctx->owner);
+    return LBM_OK;
+}
+
+int lbm_mss_to_saturation(lbm_ctx *ctx, double target, double gain, double max_rate, double tol, int check_every,
+                          int max_steps, int *steps_done)
+{
+    if (!ctx || !steps_done || !(target >= 0.0 && target <= 1.0) || !(gain > 0.0) || !(max_rate > 0.0) ||
+        !(tol > 0.0) || check_every < 1 || max_steps < 1 || !std::isfinite(gain) || !std::isfinite(max_rate))
+        return LBM_ERR_ARG;
+    if (!ctx->has_fields) return LBM_ERR_STATE;
+    int done = 0, rc = LBM_OK;
+    bool reached = false;
+    lbm_obs o;
+    while (rc == LBM_OK) {
+        rc = lbm_observables(ctx, &o);
+        if (rc != LBM_OK) break;
+        const double err = target - o.sat;
+        reached = std::fabs(err) <= tol;
+        if (reached || done >= max_steps) break;
+        rc = lbm_set_mss(ctx, std::max(-max_rate, std::min(max_rate, gain * err)));
+        const int m = std::min(check_every, max_steps - done);
+        if (rc == LBM_OK) rc = lbm_step(ctx, m);
+        done += m;
+    }
+    const int off = lbm_set_mss(ctx, 0.0);
+    *steps_done = done;
+    if (rc != LBM_OK) return rc;
+    if (off != LBM_OK) return off;
+    return reached ? LBM_OK : LBM_ERR_TIMEOUT;
 }
 
 int lbm_pressure_levels(lbm_ctx *ctx, int nlevels, const double *rho_in, const double *rho_out, int check_every,

@@ -32,7 +32,7 @@ namespace lbm {
 // waiting), largest runs first; an item is (run, column, z-chunk).  Each run
 // is a self-contained lattice whose slots, cell types, gray records and
 // fields sit at its own offsets of the batch buffers.
-template <int TX, int TY, int MINB, bool MACRO, bool HELD, class LY>
+template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY>
 __global__ void __launch_bounds__(TX *TY, MINB)
     k_fused_batch(DevParams P, const BatchRun *__restrict__ runs, int nruns, int nitems,
                   unsigned int *__restrict__ counter, const unsigned char *__restrict__ fin,
@@ -61,13 +61,14 @@ __global__ void __launch_bounds__(TX *TY, MINB)
         for (int a = 0; a < 2; ++a)
             for (int d = 0; d < 3; ++d) G.accel[a][d] = R.accel[a][d];
         for (int k = 0; k < 8; ++k) (&G.held[0][0][0])[k] = (&R.held[0][0][0])[k];
+        G.mss = R.mss;
         const int local = item - R.item0;
         const int col = local % R.ncol, chunk = local / R.ncol;
         const int za = (int)((long long)R.nz * chunk / R.zchunks);
         const int zb = (int)((long long)R.nz * (chunk + 1) / R.zchunks);
         if (za >= zb) continue;
         const LY ly = LY::make(fin + R.pop_off, fout + R.pop_off, R.n);
-        fused_item<TX, TY, MACRO, HELD>(P, G, ly, type + R.cell_off, gray + R.cell_off, macro + 6 * R.cell_off,
+        fused_item<TX, TY, MACRO, EXT>(P, G, ly, type + R.cell_off, gray + R.cell_off, macro + 6 * R.cell_off,
                                   (col % R.tiles_x) * TX, (col / R.tiles_x) * TY, za, zb, smem_raw);
     }
 }
@@ -83,10 +84,10 @@ struct TileShape {
 constexpr TileShape BATCH_TILES[] = {{32, 8, 2}, {16, 16, 2}, {32, 16, 1}};
 constexpr int N_BATCH_TILES = 3;
 
-template <int TX, int TY, int MINB, bool MACRO, bool HELD, class LY>
+template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY>
 cudaError_t prep_kernel(int *slots, int dev)
 {
-    auto kern = lbm::k_fused_batch<TX, TY, MINB, MACRO, HELD, LY>;
+    auto kern = lbm::k_fused_batch<TX, TY, MINB, MACRO, EXT, LY>;
     const size_t smem = lbm::Tiles<TX, TY>::smem();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -122,13 +123,15 @@ struct lbm_batch {
     struct Group {
         int tile;
         std::vector<int> runs;
+        std::vector<lbm::BatchRun> host;  // the item table as uploaded (runs in the order above)
         lbm::BatchRun *d_runs = nullptr;
         unsigned int *counter = nullptr;
         int nruns = 0, nitems = 0, grid = 0;
     };
     std::vector<Group> groups;
     bool groups_ok = false;
-    bool held = false;  // some run has reservoir cells: launch the march that handles them
+    bool ext = false;         // some run has reservoir cells or a mass-sink-source rate
+    bool runs_dirty = false;  // a run's reservoir densities or rate changed since the upload
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (steps, parity)
     cudaStream_t cap = nullptr;  // private stream the graphs are captured on
 };
@@ -168,6 +171,7 @@ lbm::BatchRun describe_run(const lbm_batch *b, int r, const TileShape &ts, int p
     for (int a = 0; a < 2; ++a)
         for (int d = 0; d < 3; ++d) R.accel[a][d] = (float)p.body_accel[a][d];
     for (int k = 0; k < 8; ++k) (&R.held[0][0][0])[k] = (&b->views[r]->dp.held[0][0][0])[k];
+    R.mss = b->views[r]->dp.mss;
     return R;
 }
 
@@ -211,7 +215,8 @@ int build_groups(lbm_batch *b, const std::vector<int> &subset, const std::vector
         LBM_CUDA(cudaMalloc(&g.counter, sizeof(unsigned int)));
         LBM_CUDA(cudaMemcpyAsync(g.d_runs, host.data(), host.size() * sizeof(lbm::BatchRun),
                                  cudaMemcpyHostToDevice, b->stream));
-        b->groups.push_back(g);
+        g.host = std::move(host);
+        b->groups.push_back(std::move(g));
     }
     LBM_CUDA(cudaStreamSynchronize(b->stream));
     b->groups_ok = true;
@@ -227,10 +232,10 @@ cudaError_t launch_group_t(lbm_batch *b, const lbm_batch::Group &g, bool macro)
     cudaError_t e = cudaMemsetAsync(g.counter, 0, sizeof(unsigned int), b->stream);
     if (e != cudaSuccess) return e;
     const lbm::DevParams &P = b->views[0]->dp;
-    auto kern = macro ? (b->held ? lbm::k_fused_batch<TX, TY, MINB, true, true, LY>
-                                 : lbm::k_fused_batch<TX, TY, MINB, true, false, LY>)
-                      : (b->held ? lbm::k_fused_batch<TX, TY, MINB, false, true, LY>
-                                 : lbm::k_fused_batch<TX, TY, MINB, false, false, LY>);
+    auto kern = macro ? (b->ext ? lbm::k_fused_batch<TX, TY, MINB, true, true, LY>
+                                : lbm::k_fused_batch<TX, TY, MINB, true, false, LY>)
+                      : (b->ext ? lbm::k_fused_batch<TX, TY, MINB, false, true, LY>
+                                : lbm::k_fused_batch<TX, TY, MINB, false, false, LY>);
     kern<<<g.grid, TX * TY, smem, b->stream>>>(P, g.d_runs, g.nruns, g.nitems, g.counter, fin, fout, b->type,
                                                b->gray, b->macro);
     return cudaGetLastError();
@@ -284,16 +289,31 @@ int slots_for(const lbm_batch *b, int tile, int *slots)
     return e == cudaSuccess ? LBM_OK : cuda_fail(e, "batch kernel setup");
 }
 
-// Picks the march for the runs' geometries (with or without reservoir
-// cells); a change drops the captured graphs.
-void sync_held(lbm_batch *b)
+// Picks the march for the runs (with reservoir cells or a mass-sink-source
+// rate, or neither; a change drops the captured graphs) and uploads per-run
+// parameters changed since the item tables were built.  The graphs read the
+// tables from device memory, so an upload needs no new capture.
+int sync_runs(lbm_batch *b)
 {
-    bool held = false;
-    for (auto *v : b->views) held = held || v->n_held > 0;
-    if (held != b->held) {
-        b->held = held;
+    bool ext = false;
+    for (auto *v : b->views) ext = ext || v->n_held > 0 || v->mss != 0.0;
+    if (ext != b->ext) {
+        b->ext = ext;
         free_graphs(b);
     }
+    if (b->runs_dirty && b->groups_ok) {
+        for (auto &g : b->groups) {
+            for (size_t k = 0; k < g.runs.size(); ++k) {
+                const lbm::DevParams &dp = b->views[g.runs[k]]->dp;
+                for (int q = 0; q < 8; ++q) (&g.host[k].held[0][0][0])[q] = (&dp.held[0][0][0])[q];
+                g.host[k].mss = dp.mss;
+            }
+            LBM_CUDA(cudaMemcpyAsync(g.d_runs, g.host.data(), g.host.size() * sizeof(lbm::BatchRun),
+                                     cudaMemcpyHostToDevice, b->stream));
+        }
+    }
+    b->runs_dirty = false;
+    return LBM_OK;
 }
 
 // nsteps steps of the current groups, enqueued on the stream.
@@ -443,7 +463,8 @@ int lbm_batch_step(lbm_batch *b, int nsteps)
     if (nsteps == 0) return LBM_OK;
     DeviceGuard dg(b->dev);
     if (!dg.ok) return LBM_ERR_CUDA;
-    sync_held(b);
+    int src = sync_runs(b);
+    if (src != LBM_OK) return src;
     if (!b->groups_ok) {
         std::vector<int> all(b->views.size());
         for (size_t r = 0; r < all.size(); ++r) all[r] = (int)r;
@@ -493,7 +514,8 @@ int lbm_batch_tune(lbm_batch *b, int trial_steps, int *tiles_out)
         if (!v->has_fields || v->cur != b->cur) return LBM_ERR_STATE;
     DeviceGuard dg(b->dev);
     if (!dg.ok) return LBM_ERR_CUDA;
-    sync_held(b);
+    const int src = sync_runs(b);
+    if (src != LBM_OK) return src;
     trial_steps += trial_steps & 1;  // even: the buffer parity returns
     // save the state the trials advance (populations, residual flags, fields)
     const size_t gray_bytes = (size_t)b->cells * sizeof(lbm::GrayRec), macro_bytes = 6 * (size_t)b->cells * 4;
@@ -572,6 +594,39 @@ int lbm_batch_info(lbm_batch *b, long long *cells, long long *steps, long long *
     return LBM_OK;
 }
 
+int lbm_batch_mss_to_saturation(lbm_batch *b, const double *targets, double gain, double max_rate, double tol,
+                                int check_every, int max_steps, int *steps_done)
+{
+    if (!b || !targets || !steps_done || !(gain > 0.0) || !(max_rate > 0.0) || !(tol > 0.0) || check_every < 1 ||
+        max_steps < 1 || !std::isfinite(gain) || !std::isfinite(max_rate))
+        return LBM_ERR_ARG;
+    const size_t nr = b->views.size();
+    for (size_t r = 0; r < nr; ++r)
+        if (!(targets[r] >= 0.0 && targets[r] <= 1.0)) return LBM_ERR_ARG;
+    std::vector<lbm_obs> obs(nr);
+    int done = 0, rc = LBM_OK;
+    bool reached = false;
+    while (rc == LBM_OK) {
+        rc = lbm_batch_observables(b, obs.data());
+        if (rc != LBM_OK) break;
+        reached = true;
+        for (size_t r = 0; r < nr; ++r) reached = reached && std::fabs(targets[r] - obs[r].sat) <= tol;
+        if (reached || done >= max_steps) break;
+        for (size_t r = 0; r < nr && rc == LBM_OK; ++r) {
+            const double err = targets[r] - obs[r].sat;
+            const double rate = std::fabs(err) <= tol ? 0.0 : std::max(-max_rate, std::min(max_rate, gain * err));
+            rc = lbm_set_mss(b->views[r], rate);
+        }
+        const int m = std::min(check_every, max_steps - done);
+        if (rc == LBM_OK) rc = lbm_batch_step(b, m);
+        done += m;
+    }
+    for (auto *v : b->views) lbm_set_mss(v, 0.0);
+    *steps_done = done;
+    if (rc != LBM_OK) return rc;
+    return reached ? LBM_OK : LBM_ERR_TIMEOUT;
+}
+
 int lbm_batch_step_to_steady(lbm_batch *b, int check_every, double rel_tol, int max_steps, int *steps_done)
 {
     if (!b || check_every < 1 || !(rel_tol > 0.0) || max_steps < 0) return LBM_ERR_ARG;
@@ -619,9 +674,10 @@ int lbm_batch_observables(lbm_batch *b, lbm_obs *out)
 
 }  // extern "C"
 
-// A view changed a per-run parameter (its reservoir densities): the item
-// tables, which carry them, are rebuilt before the next step.
+// A view changed a per-run parameter (reservoir densities, mass-sink-source
+// rate): the item tables, which carry them, are uploaded again before the
+// next step.
 void lbm::batch_runs_changed(lbm_batch *b)
 {
-    if (b) b->groups_ok = false;
+    if (b) b->runs_dirty = true;
 }

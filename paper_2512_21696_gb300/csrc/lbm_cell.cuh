@@ -339,6 +339,7 @@ struct Geo {
     int nx, ny, nz, n;
     float accel[2][3];
     float held[2][2][2];  // reservoir densities, as DevParams::held
+    float mss;            // mass-sink-source rate, as DevParams::mss
 };
 __device__ __forceinline__ Geo geo_of(const DevParams &P)
 {
@@ -350,6 +351,7 @@ __device__ __forceinline__ Geo geo_of(const DevParams &P)
     for (int a = 0; a < 2; ++a)
         for (int d = 0; d < 3; ++d) G.accel[a][d] = P.accel[a][d];
     for (int k = 0; k < 8; ++k) (&G.held[0][0][0])[k] = (&P.held[0][0][0])[k];
+    G.mss = P.mss;
     return G;
 }
 
@@ -362,6 +364,7 @@ struct BatchRun {
     long long pop_off;   // byte offset of the run in each population buffer
     float accel[2][3];
     float held[2][2][2];  // reservoir densities of the run
+    float mss;            // mass-sink-source rate of the run
 };
 
 // ---- rest-referenced layouts ----------------------------------------------
@@ -462,7 +465,8 @@ struct StoreRest {
 //   tgt  tgt(i): offset within a component's array where direction i goes,
 //        i n + (index of x + c_i), or opp(i) n + c when x + c_i is solid.
 template <bool MACRO, class Store, class Target>
-__device__ __forceinline__ void collide_store(const DevParams &P, const float (&acc)[2][3], uint8_t t, int c, int n,
+__device__ __forceinline__ void collide_store(const DevParams &P, const float (&acc)[2][3], float mss, uint8_t t,
+                                              int c, int n,
                                               Store &st,
                                               const CompMom M[2], const float gf[2][3], const float gAt[3],
                                               bool csf, const HessSum &hA, const HessSum &hB,
@@ -607,6 +611,13 @@ __device__ __forceinline__ void collide_store(const DevParams &P, const float (&
 
     // ---- regularised collision, written as rest population + deviations ---
     const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    // mass-sink-source: dm = m I moved from the non-wetting to the wetting
+    // component as rest equilibrium, I = max(0, (4 r_w r_n - I_b)/(1 - I_b))
+    float dm = 0.f;
+    if (mss != 0.f) {
+        const float it = __fdividef(1.0f, rt);
+        dm = mss * fmaxf((4.0f * (rw * it) * (rn * it) - P.mss_ib) * P.mss_inv, 0.f);
+    }
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
         const float om = P.omega_fac[a];
@@ -624,7 +635,7 @@ __device__ __forceinline__ void collide_store(const DevParams &P, const float (&
         const float Pyz = S[5] - ra * u[1] * u[2] + 0.5f * (u[1] * Fa[2] + Fa[1] * u[2]);
         const float trP = Pxx + Pyy + Pzz;
         // f*_0 - f_r = drho/3 - rho u^2/2 - om tr(Pi1)/2 - u.F/2
-        const float d0 = d3 - 0.5f * ra * uu - 0.5f * om * trP - 0.5f * uF;
+        const float d0 = d3 - 0.5f * ra * uu - 0.5f * om * trP - 0.5f * uF + (a == w ? dm : -dm) * (1.0f / 3.0f);
         const float res = st.rest(a, d0);
         // opposite pairs (i, i+1): cu, cF change sign, cPc does not, so
         // g_i = E + O and g_{i+1} = E - O

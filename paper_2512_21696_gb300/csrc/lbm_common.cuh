@@ -69,6 +69,8 @@ struct DevParams {
     float at_wall;         // Atwood number of the wall densities
     float rho0[2];         // shift of the 16-bit storages: f_i - w_i rho0
     float held[2][2][2];   // inlet [0] / outlet [1] densities (A, B) as float-float (hi, lo)
+    float mss;             // mass-sink-source rate m (0: off)
+    float mss_ib, mss_inv; // interface indicator: bulk value I_b = 4 r_lo r_hi and 1/(1 - I_b)
     int storage;           // enum lbm_storage
     Curve curve[MAX_TYPES];
 };

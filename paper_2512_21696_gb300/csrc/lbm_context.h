@@ -15,6 +15,7 @@ struct lbm_ctx {
     lbm_params p;
     double rho_held[2][2];       // densities (A, B) of the inlet [0] and outlet [1] cells
     long long n_held = 0;        // number of inlet / outlet cells in the geometry
+    double mss = 0.0;            // mass-sink-source rate (lbm_set_mss)
     struct lbm_batch *owner = nullptr;  // the batch of a view
     int dev = 0;
     cudaStream_t stream = nullptr;

@@ -397,6 +397,12 @@ __global__ void __launch_bounds__(256) k2_collide(DevParams P, const float *__re
 
     // ---- regularised collision and push --------------------------------------
     const float uu = u[0] * u[0] + u[1] * u[1];
+    // mass-sink-source: dm = m I from the non-wetting to the wetting component
+    float dm = 0.f;
+    if (!held && P.mss != 0.f) {
+        const float it = __fdividef(1.0f, rt);
+        dm = P.mss * fmaxf((4.0f * (rw * it) * (rn * it) - P.mss_ib) * P.mss_inv, 0.f);
+    }
     auto tgt = [&](int i) -> size_t {
         return (wall & (1u << i)) ? (size_t)opp(i) * n + c : (size_t)i * n + nbi[i];
     };
@@ -412,7 +418,8 @@ __global__ void __launch_bounds__(256) k2_collide(DevParams P, const float *__re
         const float Pyy = S[a][1] - d3 - ra * u[1] * u[1] + u[1] * Fa[1];
         const float Pxy = S[a][2] - ra * u[0] * u[1] + 0.5f * (u[0] * Fa[1] + Fa[0] * u[1]);
         // f*_0 - f_r = w_0 drho - (2/3)(rho u^2 + om tr(Pi1) + u.F)
-        const float d0 = (4.0f / 9.0f) * dr[a].hi - (2.0f / 3.0f) * (ra * uu + om * (Pxx + Pyy) + uF);
+        const float d0 = (4.0f / 9.0f) * (dr[a].hi + (a == w ? dm : -dm)) -
+                         (2.0f / 3.0f) * (ra * uu + om * (Pxx + Pyy) + uF);
         const float xq = d0 * FIX_ONE;
         const float qf = rintf(xq);
         float *fo = fout + (size_t)a * Q * n;

@@ -11,7 +11,7 @@
 
 namespace lbm {
 
-template <int TX, int TY, int MINB, bool MACRO, bool HELD, class LY>
+template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY>
 __global__ void __launch_bounds__(TX *TY, MINB)
     k_fused(DevParams P, int zchunks, LY ly, const uint8_t *__restrict__ type, GrayRec *__restrict__ gray,
             float *__restrict__ macro)
@@ -25,16 +25,16 @@ __global__ void __launch_bounds__(TX *TY, MINB)
         const int za = (int)((long long)P.nz * chunk / zchunks);
         const int zb = (int)((long long)P.nz * (chunk + 1) / zchunks);
         if (za >= zb) continue;
-        fused_item<TX, TY, MACRO, HELD>(P, G, ly, type, gray, macro, (col % tiles_x) * TX, (col / tiles_x) * TY, za,
+        fused_item<TX, TY, MACRO, EXT>(P, G, ly, type, gray, macro, (col % tiles_x) * TX, (col / tiles_x) * TY, za,
                                         zb, smem_raw);
     }
 }
 
 // ---------------------------------------------------------------------------
-template <int TX, int TY, int MINB, bool MACRO, bool HELD, class LY>
+template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY>
 static cudaError_t launch_fused_t(lbm_ctx *ctx, LY ly)
 {
-    auto kern = k_fused<TX, TY, MINB, MACRO, HELD, LY>;
+    auto kern = k_fused<TX, TY, MINB, MACRO, EXT, LY>;
     const size_t smem = Tiles<TX, TY>::smem();
     // launch configuration, resolved once per device
     static int cached_slots[64] = {};  // resident CTAs per device
@@ -63,12 +63,12 @@ static cudaError_t launch_fused_t(lbm_ctx *ctx, LY ly)
     return cudaGetLastError();
 }
 
-// Geometries with reservoir cells run the instantiation that handles them;
-// the others keep the plain march.
+// Geometries with reservoir cells, or a mass-sink-source rate, run the
+// instantiation that handles them; the others keep the plain march.
 template <int TX, int TY, int MINB, class LY>
 static cudaError_t launch_fused_tile(lbm_ctx *ctx, bool write_macro, LY ly)
 {
-    if (ctx->n_held > 0)
+    if (ctx->n_held > 0 || ctx->mss != 0.0)
         return write_macro ? launch_fused_t<TX, TY, MINB, true, true>(ctx, ly)
                            : launch_fused_t<TX, TY, MINB, false, true>(ctx, ly);
     return write_macro ? launch_fused_t<TX, TY, MINB, true, false>(ctx, ly)

@@ -57,10 +57,10 @@ __device__ __forceinline__ int ring3(int p) { return ((p % 3) + 3) % 3; }
 
 // One work item: the TX x TY columns at (x0, y0) over planes [za, zb) of the
 // lattice of shape G (G.n is the slot stride of ly, type, gray and macro),
-// physics P.  HELD compiles in the reservoir (inlet / outlet) cells; without
-// it those cell types are not expected.  Ends with a block barrier, so the
-// rings can be reused at once.
-template <int TX, int TY, bool MACRO, bool HELD, class LY>
+// physics P.  EXT compiles in the reservoir (inlet / outlet) cells and the
+// mass-sink-source term; without it neither is expected.  Ends with a block
+// barrier, so the rings can be reused at once.
+template <int TX, int TY, bool MACRO, bool EXT, class LY>
 __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, const LY &ly,
                                            const uint8_t *__restrict__ type,
                                            GrayRec *__restrict__ gray, float *__restrict__ macro, int x0, int y0,
@@ -112,7 +112,7 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
             if (me.type != CELL_SOLID) {
                 g = wrap_coord(x0 - 1 + dx, G.nx, P.per[0]) +
                     G.nx * (wrap_coord(y0 - 1 + dy, G.ny, P.per[1]) + G.ny * gz);
-                const bool held = HELD && is_held(me.type);
+                const bool held = EXT && is_held(me.type);
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
                     const int f0 = a ? me.f0B : me.f0A;
@@ -192,7 +192,7 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
             M[a] = finish_moments_d(p, f0i[a], a ? ff{dc.drB, dc.loB} : ff{dc.drA, dc.loA});
         }
         const uint8_t t = (uint8_t)me.type;
-        const bool held = HELD && is_held(t);
+        const bool held = EXT && is_held(t);
         if (held) {  // reservoir: held density at rest, no force
             M[0] = held_moments(held_rho(G.held, t, 0), ff{dc.drA, dc.loA});
             M[1] = held_moments(held_rho(G.held, t, 1), ff{dc.drB, dc.loB});
@@ -233,7 +233,8 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
                 if (held) gf[a][d] = 0.f;
             }
         StoreRest<LY> st{ly, c, {f0i[0], f0i[1]}};
-        collide_store<MACRO>(P, acc, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
+        collide_store<MACRO>(P, acc, (EXT && !held) ? G.mss : 0.f, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro,
+                             tgt);
     };
 
     load_raw(za - 2);

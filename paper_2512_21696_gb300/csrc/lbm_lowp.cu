@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
                     if (held) gf[a][d] = 0.f;
                 }
             StoreLP<H> st{fout, n, c, {r[0] * (1.0f / 3.0f), r[1] * (1.0f / 3.0f)}, {P.rho0[0], P.rho0[1]}, {0.f, 0.f}};
-            collide_store<MACRO>(P, acc, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
+            collide_store<MACRO>(P, acc, held ? 0.f : P.mss, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
         };
 
         densities(za - 1);

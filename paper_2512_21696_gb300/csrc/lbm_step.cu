@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(256) k_collide(DevParams P, const float *__res
             if (held) gf[a][d] = 0.f;
         }
     StoreRest<LayF32> st{LayF32{fin, fout, n}, c, {f0i[0], f0i[1]}};
-    collide_store<MACRO>(P, acc, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
+    collide_store<MACRO>(P, acc, held ? 0.f : P.mss, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
 }
 
 // ---------------------------------------------------------------------------

@@ -22,7 +22,8 @@ __all__ = [
     "lbm_destroy", "lbm_set_constitutive", "lbm_set_geometry", "lbm_init_fields", "lbm_step",
     "lbm_observables", "lbm_get_fields", "lbm_get_static", "lbm_save_state", "lbm_load_state",
     "lbm_profile", "lbm_profile_read", "lbm_launch_count", "lbm_abi_version", "lbm_observables_noalloc", "lbm_set_kernel",
-    "lbm_set_pressure", "lbm_pressure_levels", "LBM_CELL_INLET", "LBM_CELL_OUTLET",
+    "lbm_set_pressure", "lbm_pressure_levels", "LBM_CELL_INLET", "LBM_CELL_OUTLET", "lbm_set_mss",
+    "lbm_mss_to_saturation", "lbm_batch_mss_to_saturation",
     "LBM_CELL_PORE", "LBM_CELL_SOLID", "LBM_CELL_GRAY", "LBM_STORAGE_F32", "LBM_STORAGE_F16S",
     "LBM_STORAGE_BF16S",
 ]
@@ -185,6 +186,34 @@ def lbm_set_pressure(ctx: LbmContext, rho_in, rho_out) -> None:
     a = (C.c_double * 2)(*[float(v) for v in rho_in])
     b = (C.c_double * 2)(*[float(v) for v in rho_out])
     _check(L.load().lbm_set_pressure(ctx.handle, a, b), "lbm_set_pressure")
+
+
+def lbm_set_mss(ctx: LbmContext, rate: float) -> None:
+    """Mass-sink-source rate (wetting component gains rate * I per step) from the next step."""
+    _check(L.load().lbm_set_mss(ctx.handle, float(rate)), "lbm_set_mss")
+
+
+def lbm_mss_to_saturation(ctx: LbmContext, target: float, gain: float, max_rate: float, tol: float,
+                          check_every: int, max_steps: int):
+    """Drive the saturation to target with the mass-sink-source; returns (reached, steps)."""
+    done = C.c_int()
+    code = L.load().lbm_mss_to_saturation(ctx.handle, float(target), float(gain), float(max_rate), float(tol),
+                                          int(check_every), int(max_steps), C.byref(done))
+    if code not in (L.LBM_OK, L.LBM_ERR_TIMEOUT):
+        _check(code, "lbm_mss_to_saturation")
+    return code == L.LBM_OK, done.value
+
+
+def lbm_batch_mss_to_saturation(batch, targets, gain: float, max_rate: float, tol: float, check_every: int,
+                                max_steps: int):
+    """Every run of a batch to its own target saturation; returns (reached, steps)."""
+    t = (C.c_double * len(targets))(*[float(v) for v in targets])
+    done = C.c_int()
+    code = L.load().lbm_batch_mss_to_saturation(batch.handle, t, float(gain), float(max_rate), float(tol),
+                                                int(check_every), int(max_steps), C.byref(done))
+    if code not in (L.LBM_OK, L.LBM_ERR_TIMEOUT):
+        _check(code, "lbm_batch_mss_to_saturation")
+    return code == L.LBM_OK, done.value
 
 
 def lbm_pressure_levels(ctx: LbmContext, levels, check_every: int, sat_tol: float, max_steps: int):

@@ -14,7 +14,7 @@ from paper_2512_21696_gb300 import synth
 DEFAULTS = dict(G=0.0, kappa=0.0, tau=(1.0, 1.0), accel=((0, 0, 0), (0, 0, 0)), csf_everywhere=0,
                 rho_wall=(0.515, 0.515), wet=1, rho_hi=1.0, rho_lo=0.03, periodic=(1, 1, 1),
                 s_lo=0.1, s_hi=0.9, at_cut=0.95, kr_min=1e-6, c_g=1.0, phi_avg=(0.515, 0.515),
-                phi_max=(1.0, 1.0), held=None, lattice="d3q19")
+                phi_max=(1.0, 1.0), held=None, lattice="d3q19", mss=0.0)
 CURVE = dict(kc_d=1.0, pd=0.02, lam=2.0, swr=0.15, nw=3.0, nn=2.0, phi_ref=0.35, f_max=3.5,
              f_min=0.575, aniso=1.0, thomeer_g=0.0)
 
@@ -75,7 +75,7 @@ def oracle_params(case: Case):
                          phi_avg=s["phi_avg"], phi_max=s["phi_max"], csf_everywhere=s["csf_everywhere"],
                          rho_wall=s["rho_wall"], accel=s["accel"], wet=s["wet"], rho_hi=s["rho_hi"],
                          rho_lo=s["rho_lo"], s_lo=s["s_lo"], s_hi=s["s_hi"], at_cut=s["at_cut"],
-                         eps_n=s["eps_n"], kr_min=s["kr_min"], c_g=s["c_g"], lattice=s["lattice"])
+                         eps_n=s["eps_n"], kr_min=s["kr_min"], c_g=s["c_g"], lattice=s["lattice"], mss=s["mss"])
 
 
 def run_gpu(case: Case, steps: int, device_arrays=False, path=0, tile=0, **extra):
@@ -99,6 +99,8 @@ def run_gpu(case: Case, steps: int, device_arrays=False, path=0, tile=0, **extra
             lbm.lbm_init_fields(ctx, case.rhoA32, case.rhoB32, case.u32)
         if case.s["held"] is not None:
             lbm.lbm_set_pressure(ctx, *case.s["held"])
+        if case.s["mss"]:
+            lbm.lbm_set_mss(ctx, case.s["mss"])
         lbm.lbm_step(ctx, steps)
         fields = lbm.lbm_get_fields(ctx)
         obs = lbm.lbm_observables(ctx, check=False)
