@@ -390,7 +390,8 @@ LBM_API int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int ckp
  *   largest component over the last chunk (steady flow: the permeability
  *   K = <u> nu / g is then read at steady state), or until max_steps; returns
  *   LBM_OK when steady, LBM_ERR_TIMEOUT when max_steps ran out; steps_done
- *   (may be NULL) receives the steps taken.  Synchronous.
+ *   (may be NULL) receives the steps taken.  Runs whose fields turned
+ *   non-finite are left out of the test.  Synchronous.
  * lbm_batch_info: total cells, steps taken, kernels launched by
  *   lbm_batch_step, and the number of launches per step. */
 typedef struct lbm_batch lbm_batch;
@@ -406,7 +407,9 @@ LBM_API int lbm_batch_step_to_steady(lbm_batch *b, int check_every, double rel_t
 /* lbm_mss_to_saturation for every run of a batch at once, targets[nruns]
  * (host array): each run has its own rate; the batch steps until every run
  * is within tol of its target at a check (LBM_OK) or max_steps ran
- * (LBM_ERR_TIMEOUT).  All rates are 0 on return.  Synchronous. */
+ * (LBM_ERR_TIMEOUT).  Runs whose fields turned non-finite are left out (rate
+ * 0; lbm_batch_observables reports them).  All rates are 0 on return.
+ * Synchronous. */
 LBM_API int lbm_batch_mss_to_saturation(lbm_batch *b, const double *targets, double gain, double max_rate,
                                         double tol, int check_every, int max_steps, int *steps_done);
 

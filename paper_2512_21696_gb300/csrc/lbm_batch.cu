@@ -608,13 +608,17 @@ int lbm_batch_mss_to_saturation(lbm_batch *b, const double *targets, double gain
     bool reached = false;
     while (rc == LBM_OK) {
         rc = lbm_batch_observables(b, obs.data());
+        if (rc == LBM_ERR_NUMERIC) rc = LBM_OK;  // runs with non-finite fields are left out below
         if (rc != LBM_OK) break;
         reached = true;
-        for (size_t r = 0; r < nr; ++r) reached = reached && std::fabs(targets[r] - obs[r].sat) <= tol;
+        for (size_t r = 0; r < nr; ++r)
+            reached = reached && (obs[r].nan_count > 0 || std::fabs(targets[r] - obs[r].sat) <= tol);
         if (reached || done >= max_steps) break;
         for (size_t r = 0; r < nr && rc == LBM_OK; ++r) {
             const double err = targets[r] - obs[r].sat;
-            const double rate = std::fabs(err) <= tol ? 0.0 : std::max(-max_rate, std::min(max_rate, gain * err));
+            const double rate = (obs[r].nan_count > 0 || std::fabs(err) <= tol)
+                                    ? 0.0
+                                    : std::max(-max_rate, std::min(max_rate, gain * err));
             rc = lbm_set_mss(b->views[r], rate);
         }
         const int m = std::min(check_every, max_steps - done);
@@ -633,7 +637,7 @@ int lbm_batch_step_to_steady(lbm_batch *b, int check_every, double rel_tol, int 
     const size_t nr = b->views.size();
     std::vector<lbm_obs> prev(nr), cur(nr);
     int rc = lbm_batch_observables(b, prev.data());
-    if (rc != LBM_OK) return rc;
+    if (rc != LBM_OK && rc != LBM_ERR_NUMERIC) return rc;
     int done = 0;
     bool steady = false;
     while (!steady && done < max_steps) {
@@ -642,9 +646,10 @@ int lbm_batch_step_to_steady(lbm_batch *b, int check_every, double rel_tol, int 
         if (rc != LBM_OK) return rc;
         done += k;
         rc = lbm_batch_observables(b, cur.data());
-        if (rc != LBM_OK) return rc;
+        if (rc != LBM_OK && rc != LBM_ERR_NUMERIC) return rc;
         steady = true;
-        for (size_t r = 0; r < nr && steady; ++r)
+        for (size_t r = 0; r < nr && steady; ++r) {
+            if (cur[r].nan_count > 0) continue;  // non-finite runs are left out (see lbm_batch_observables)
             for (int d = 0; d < 3; ++d) {
                 const double a = cur[r].flux_vol[d], p = prev[r].flux_vol[d];
                 const double scale = std::max({std::fabs(cur[r].flux_vol[0]), std::fabs(cur[r].flux_vol[1]),
@@ -654,6 +659,7 @@ int lbm_batch_step_to_steady(lbm_batch *b, int check_every, double rel_tol, int 
                     break;
                 }
             }
+        }
         prev.swap(cur);
     }
     if (steps_done) *steps_done = done;
