@@ -299,6 +299,18 @@ LBM_API int lbm_pressure_levels(lbm_ctx *ctx, int nlevels, const double *rho_in,
  * Returns LBM_ERR_NUMERIC when nan_count > 0 (out is still filled). */
 LBM_API int lbm_observables(lbm_ctx *ctx, lbm_obs *out);
 
+/* Asynchronous observables for monitoring loops: enqueues the reductions of
+ * the current fields and the copy of their raw sums into raw[0..15] on the
+ * context's stream and returns; raw[16] receives the step count at once.
+ * raw: LBM_OBS_RAW doubles of host memory (pinned, so that the copy does not
+ * wait) that stays valid until the stream has passed the copy; several calls
+ * may be in flight, each with its own raw.  lbm_obs_decode turns raw into
+ * lbm_obs (host arithmetic only) after the stream passed the copy, and
+ * returns LBM_ERR_NUMERIC when nan_count > 0 as lbm_observables does. */
+#define LBM_OBS_RAW 17
+LBM_API int lbm_observables_async(lbm_ctx *ctx, double *raw);
+LBM_API int lbm_obs_decode(lbm_ctx *ctx, const double *raw, lbm_obs *out);
+
 /* Current fields: rhoA, rhoB [ncell], u [3][ncell], sw [ncell] (effective
  * water saturation incl. residual amounts); any pointer may be NULL.  Solid
  * cells read 0. */
@@ -428,7 +440,7 @@ LBM_API int lbm_launch_count(lbm_ctx *ctx, long long *count);
  *             Shan-Chen coupling of the pressure p = (rhoA+rhoB)/3 + G rhoA rhoB,
  * on `stream` (cudaStream_t, NULL = legacy default), and writes *out (host;
  * out->step is 0).  Synchronises the stream.
- * Scratch: a file-scope device array of 131,200 bytes that every GPU loading
+ * Scratch: a file-scope device array of 77,952 bytes that every GPU loading
  * this library holds until exit.  The first call on a device resolves that
  * array's address (cudaGetSymbolAddress); make that first call before any
  * stream capture.  All calls share the array: calls that overlap on the GPU

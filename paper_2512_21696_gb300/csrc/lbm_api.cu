@@ -518,8 +518,26 @@ int lbm_observables(lbm_ctx *ctx, lbm_obs *out)
     if (!ctx->has_fields) return LBM_ERR_STATE;
     DeviceGuard g(ctx->dev);
     if (!g.ok) return LBM_ERR_CUDA;
-    double v[lbm::NOBS_HOST];
+    double v[LBM_OBS_RAW];
     LBM_CUDA(lbm::launch_observables(ctx, v));
+    v[lbm::NOBS_HOST] = (double)ctx->steps;
+    return lbm_obs_decode(ctx, v, out);
+}
+
+int lbm_observables_async(lbm_ctx *ctx, double *raw)
+{
+    if (!ctx || !raw) return LBM_ERR_ARG;
+    if (!ctx->has_fields) return LBM_ERR_STATE;
+    DeviceGuard g(ctx->dev);
+    if (!g.ok) return LBM_ERR_CUDA;
+    raw[lbm::NOBS_HOST] = (double)ctx->steps;
+    LBM_CUDA(lbm::launch_observables(ctx, raw, false));
+    return LBM_OK;
+}
+
+int lbm_obs_decode(lbm_ctx *ctx, const double *v, lbm_obs *out)
+{
+    if (!ctx || !v || !out) return LBM_ERR_ARG;
     const lbm_params &p = ctx->p;
     out->mass[0] = v[0];
     out->mass[1] = v[1];
@@ -529,7 +547,7 @@ int lbm_observables(lbm_ctx *ctx, lbm_obs *out)
     out->max_u = v[8];
     out->dp = (v[10] > 0 ? v[9] / v[10] : 0.0) - (v[12] > 0 ? v[11] / v[12] : 0.0);
     out->nan_count = (long long)v[13];
-    out->step = ctx->steps;
+    out->step = (long long)v[lbm::NOBS_HOST];
     return out->nan_count > 0 ? LBM_ERR_NUMERIC : LBM_OK;
 }
 

@@ -71,6 +71,8 @@ cudaError_t launch_d2q9_init(lbm_ctx *ctx, const float *rhoA, const float *rhoB,
 cudaError_t launch_d2q9_step(lbm_ctx *ctx, bool write_macro);
 cudaError_t launch_geometry(lbm_ctx *ctx, const uint8_t *ptype);
 cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16);
+// The same without the final synchronisation (the copy is left in flight).
+cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16, bool sync);
 cudaError_t launch_static_out(lbm_ctx *ctx, float *kinv6, float *pcs, float *swirr, float *sores);
 
 // Rest-referenced 16-bit layout views of population buffers bi (in) and bo

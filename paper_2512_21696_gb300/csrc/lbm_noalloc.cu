@@ -9,7 +9,7 @@
 // instead of context-owned memory.
 //
 // The array is g_obs_scratch below: (OBS_MAX_BLOCKS + 1) * NOBS doubles =
-// 131,200 bytes, which every GPU that loads this library holds until the
+// 77,952 bytes, which every GPU that loads this library holds until the
 // process exits.  Its device address is resolved once per device with
 // cudaGetSymbolAddress by the first call on that device (host code must not
 // use the symbol itself: on the host it only names a stand-in).  Each call

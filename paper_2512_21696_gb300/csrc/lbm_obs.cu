@@ -1,9 +1,12 @@
 // Observables of the current fields (FP64 reductions) and read-back of the
 // gray-cell geometry results.
 //
-// k_obs_partial: grid-stride pass, per-thread FP64 accumulators, warp-shuffle
-//                and shared-memory block reduction, one row of partials per
-//                block in the reduction scratch;
+// k_obs_partial: grid-stride pass, per-thread float-float accumulators
+//                (error-free FP32 sums, about 48 bits: FP64 arithmetic runs at
+//                a small fraction of the FP32 rate on this part), converted
+//                to FP64 once per thread for the warp-shuffle and
+//                shared-memory block reduction, one row of partials per block
+//                in the reduction scratch;
 // k_obs_final:   one block sums the rows in a fixed order (deterministic).
 #include <cfloat>
 
@@ -50,42 +53,53 @@ __global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs 
                                                            double *__restrict__ partial)
 {
     __shared__ double sh[NOBS * 32];
-    double acc[NOBS];
+    // slots 0-7, 9, 11 summed in float-float; 10, 12, 13 are counts
+    constexpr int NS = 10;
+    constexpr int slot_of[NS] = {0, 1, 2, 3, 4, 5, 6, 7, 9, 11};
+    ff s[NS];
 #pragma unroll
-    for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NS; ++k) s[k] = ff{0.f, 0.f};
+    int cin = 0, cout = 0, bad = 0;
     const int n = P.n;
     float umax = 0.0f;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const uint8_t t = type[c];
         if (t == CELL_SOLID) continue;
-        // per-cell terms in FP32 (products of FP32 fields, one rounding each),
-        // every sum in FP64; FP64 is a small fraction of the FP32 rate here
+        // per-cell terms in FP32 (products of FP32 fields, one rounding each)
         const float ra = macro[c], rb = macro[(size_t)n + c];
         const float u0 = macro[(size_t)2 * n + c], u1 = macro[(size_t)3 * n + c], u2 = macro[(size_t)4 * n + c];
         const float sw = macro[(size_t)5 * n + c];
         if (!isfinite(ra) || !isfinite(rb) || !isfinite(u0) || !isfinite(u1) || !isfinite(u2)) {
-            acc[13] += 1.0;
+            ++bad;
             continue;
         }
         const int x = c % P.nx, y = (c / P.nx) % P.ny, z = c / (P.nx * P.ny);
-        acc[0] += (double)ra;
-        acc[1] += (double)rb;
+        s[0] = ff_add_f(s[0], ra);
+        s[1] = ff_add_f(s[1], rb);
         // saturation weight: phi in gray cells, 1 in pores, reservoirs left out
         const float phc = t == CELL_GRAY ? phi[c] : (t == CELL_PORE ? 1.0f : 0.0f);
-        acc[2] += (double)(phc * sw);
-        acc[3] += (double)phc;
-        if (x == P.nx - 1) acc[4] += (double)u0;
-        acc[5] += (double)u0;
-        acc[6] += (double)u1;
-        acc[7] += (double)u2;
+        s[2] = ff_add_f(s[2], phc * sw);
+        s[3] = ff_add_f(s[3], phc);
+        if (x == P.nx - 1) s[4] = ff_add_f(s[4], u0);
+        s[5] = ff_add_f(s[5], u0);
+        s[6] = ff_add_f(s[6], u1);
+        s[7] = ff_add_f(s[7], u2);
         umax = fmaxf(umax, sqrtf(u0 * u0 + u1 * u1 + u2 * u2));
         const float dx = x - (float)O.cx, dy = y - (float)O.cy, dz = z - (float)O.cz;
         const float r2 = dx * dx + dy * dy + dz * dz;
         const float pr = (ra + rb) * (1.0f / 3.0f) + (float)O.G * ra * rb;
-        if (r2 < (float)O.rin2) { acc[9] += (double)pr; acc[10] += 1.0; }
-        if (r2 > (float)O.rout2) { acc[11] += (double)pr; acc[12] += 1.0; }
+        if (r2 < (float)O.rin2) { s[8] = ff_add_f(s[8], pr); ++cin; }
+        if (r2 > (float)O.rout2) { s[9] = ff_add_f(s[9], pr); ++cout; }
     }
+    double acc[NOBS];
+#pragma unroll
+    for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) acc[slot_of[k]] = (double)s[k].hi + (double)s[k].lo;
     acc[8] = (double)umax;
+    acc[10] = (double)cin;
+    acc[12] = (double)cout;
+    acc[13] = (double)bad;
     block_reduce(acc, sh);
     if (threadIdx.x == 0)
         for (int k = 0; k < NOBS; ++k) partial[(size_t)blockIdx.x * NOBS + k] = acc[k];
@@ -111,13 +125,16 @@ __global__ void __launch_bounds__(OBS_BLOCK) k_obs_final(const double *__restric
 
 int obs_blocks(int n)
 {
-    int b = (n + OBS_BLOCK - 1) / OBS_BLOCK;
+    // a few resident blocks per SM; each thread then sums tens of cells
+    int b = (n + 8 * OBS_BLOCK - 1) / (8 * OBS_BLOCK);
     return b < OBS_MAX_BLOCKS ? (b < 1 ? 1 : b) : OBS_MAX_BLOCKS;
 }
 
 // Fills host_out16 (synchronises the stream).  red must hold
 // (obs_blocks(n) + 1) * NOBS doubles.
-cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16)
+cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16) { return launch_observables(ctx, host_out16, true); }
+
+cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16, bool sync)
 {
     const lbm_params &p = ctx->p;
     ObsArgs O;
@@ -142,7 +159,7 @@ cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16)
     if (err != cudaSuccess) return err;
     err = cudaMemcpyAsync(host_out16, out, NOBS * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (err != cudaSuccess) return err;
-    return cudaStreamSynchronize(ctx->stream);
+    return sync ? cudaStreamSynchronize(ctx->stream) : cudaSuccess;
 }
 
 __global__ void k_static_out(int n, const uint8_t *__restrict__ type, const GrayRec *__restrict__ gray,

@@ -11,7 +11,7 @@ constexpr int NOBS = 16;
 //        12 count outside; 13 non-finite count
 constexpr int SLOT_MAX = 8;
 constexpr int OBS_BLOCK = 256;
-constexpr int OBS_MAX_BLOCKS = 1024;
+constexpr int OBS_MAX_BLOCKS = 608;
 
 struct ObsArgs {
     double cx, cy, cz, rin2, rout2, G;

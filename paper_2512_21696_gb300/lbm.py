@@ -23,7 +23,8 @@ __all__ = [
     "lbm_observables", "lbm_get_fields", "lbm_get_static", "lbm_save_state", "lbm_load_state",
     "lbm_profile", "lbm_profile_read", "lbm_launch_count", "lbm_abi_version", "lbm_observables_noalloc", "lbm_set_kernel",
     "lbm_set_pressure", "lbm_pressure_levels", "LBM_CELL_INLET", "LBM_CELL_OUTLET", "lbm_set_mss",
-    "lbm_mss_to_saturation", "lbm_batch_mss_to_saturation",
+    "lbm_mss_to_saturation", "lbm_batch_mss_to_saturation", "lbm_observables_async", "lbm_obs_decode",
+    "LBM_OBS_RAW",
     "LBM_CELL_PORE", "LBM_CELL_SOLID", "LBM_CELL_GRAY", "LBM_STORAGE_F32", "LBM_STORAGE_F16S",
     "LBM_STORAGE_BF16S",
 ]
@@ -230,13 +231,34 @@ def lbm_pressure_levels(ctx: LbmContext, levels, check_every: int, sat_tol: floa
     return code == L.LBM_OK, list(sat), list(steps)
 
 
+LBM_OBS_RAW = L.LBM_OBS_RAW
+
+
+def lbm_observables_async(ctx: LbmContext, raw_ptr: int) -> None:
+    """Enqueue the observables into LBM_OBS_RAW doubles of (pinned) host memory at raw_ptr."""
+    _check(L.load().lbm_observables_async(ctx.handle, C.c_void_p(int(raw_ptr))), "lbm_observables_async")
+
+
+def lbm_obs_decode(ctx: LbmContext, raw_ptr: int, check: bool = True) -> dict:
+    """Observables from raw sums written by lbm_observables_async (after the stream passed the copy)."""
+    o = L.lbm_obs()
+    code = L.load().lbm_obs_decode(ctx.handle, C.c_void_p(int(raw_ptr)), C.byref(o))
+    if code not in (L.LBM_OK, L.LBM_ERR_NUMERIC) or (check and code != L.LBM_OK):
+        raise LbmError(code, "lbm_obs_decode")
+    return _obs_dict(o)
+
+
+def _obs_dict(o) -> dict:
+    return dict(mass=(o.mass[0], o.mass[1]), sat=o.sat, flux_out=o.flux_out,
+                flux_vol=tuple(o.flux_vol), max_u=o.max_u, dp=o.dp, nan_count=o.nan_count, step=o.step)
+
+
 def lbm_observables(ctx: LbmContext, check: bool = True) -> dict:
     o = L.lbm_obs()
     code = L.load().lbm_observables(ctx.handle, C.byref(o))
     if code not in (L.LBM_OK, L.LBM_ERR_NUMERIC) or (check and code != L.LBM_OK):
         raise LbmError(code, "lbm_observables")
-    return dict(mass=(o.mass[0], o.mass[1]), sat=o.sat, flux_out=o.flux_out,
-                flux_vol=tuple(o.flux_vol), max_u=o.max_u, dp=o.dp, nan_count=o.nan_count, step=o.step)
+    return _obs_dict(o)
 
 
 def lbm_get_fields(ctx: LbmContext, rhoA=None, rhoB=None, u=None, sw=None):

@@ -255,3 +255,33 @@ def test_host_injected_faults_are_reported():
         assert lbm.lbm_observables(ctx)["nan_count"] == 0
     finally:
         ctx.close()
+
+
+def test_async_observables_equal_the_synchronous_ones():
+    """lbm_observables_async + lbm_obs_decode: the same values as
+    lbm_observables for every step of a loop that never synchronises."""
+    import torch
+    from paper_2512_21696_gb300 import lbm
+    case = LC.mixed_features(seed=31)
+    ctx = lbm.lbm_create(LC.gpu_params(case))
+    try:
+        for k, cv in enumerate(case.curves):
+            lbm.lbm_set_constitutive(ctx, k, lbm.lbm_default_constitutive(
+                kc_d=cv["kc_d"], pd=cv["pd"], lam=cv["lam"], swr=cv["swr"], nw=cv["nw"], nn=cv["nn"],
+                phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"]))
+        lbm.lbm_set_geometry(ctx, case.cell, case.phi32, case.ptype)
+        lbm.lbm_init_fields(ctx, case.rhoA32, case.rhoB32, case.u32)
+        state = lbm.lbm_save_state(ctx)
+        raw = torch.zeros((6, lbm.LBM_OBS_RAW), dtype=torch.float64).pin_memory()
+        row = raw.stride(0) * raw.element_size()
+        for k in range(6):
+            lbm.lbm_step(ctx, 1)
+            lbm.lbm_observables_async(ctx, raw.data_ptr() + k * row)
+        torch.cuda.synchronize()
+        got = [lbm.lbm_obs_decode(ctx, raw.data_ptr() + k * row) for k in range(6)]
+        lbm.lbm_load_state(ctx, state)
+        for k in range(6):
+            lbm.lbm_step(ctx, 1)
+            assert lbm.lbm_observables(ctx) == got[k]
+    finally:
+        ctx.close()
