@@ -77,7 +77,7 @@ extern "C" LBM_API int lbm_observables_noalloc(const float *fields, const uint8_
     double *final_row = scratch + (size_t)lbm::OBS_MAX_BLOCKS * lbm::NOBS;
     cudaStream_t s = (cudaStream_t)stream;
     lbm::k_obs_partial<<<nb, lbm::OBS_BLOCK, 0, s>>>(P, O, type, phi, fields, partial);
-    lbm::k_obs_final<<<1, lbm::OBS_BLOCK, 0, s>>>(partial, nb, final_row);
+    lbm::k_obs_final<<<1, lbm::OBS_FINAL_THREADS, 0, s>>>(partial, nb, final_row);
     if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
     double v[lbm::NOBS];
     if (cudaMemcpyAsync(v, final_row, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LBM_ERR_CUDA;

@@ -7,7 +7,9 @@
 //                to FP64 once per thread for the warp-shuffle and
 //                shared-memory block reduction, one row of partials per block
 //                in the reduction scratch;
-// k_obs_final:   one block sums the rows in a fixed order (deterministic).
+// k_obs_final:   one block, one warp per slot: each lane sums a fixed
+//                subset of the rows, then the warp combines the lanes in a
+//                fixed order (deterministic), in FP64.
 #include <cfloat>
 
 #include "lbm_context.h"
@@ -26,24 +28,24 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-// Reduce acc[NOBS] over the block; thread 0 gets the result.
-__device__ void block_reduce(double acc[NOBS], double *sh /* [NOBS][32] */)
+// float-float sum over the warp (lane 0 gets it)
+__device__ __forceinline__ ff warp_sum_ff(ff v)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NOBS; ++k) {
-        double v = (k == SLOT_MAX) ? warp_max(acc[k]) : warp_sum(acc[k]);
-        if (lane == 0) sh[k * 32 + warp] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+        const ff w = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+        v = ff_add(v, w);
     }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int k = 0; k < NOBS; ++k) {
-            double v = lane < nw ? sh[k * 32 + lane] : (k == SLOT_MAX ? 0.0 : 0.0);
-            v = (k == SLOT_MAX) ? warp_max(v) : warp_sum(v);
-            acc[k] = v;
-        }
-    }
+    return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max_f(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
 }
 
 __global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs O,
@@ -62,6 +64,9 @@ __global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs 
     int cin = 0, cout = 0, bad = 0;
     const int n = P.n;
     float umax = 0.0f;
+    // the probe in FP32, converted once (a conversion from FP64 runs on the FP64 pipe)
+    const float pcx = (float)O.cx, pcy = (float)O.cy, pcz = (float)O.cz;
+    const float rin2 = (float)O.rin2, rout2 = (float)O.rout2, Gf = (float)O.G;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const uint8_t t = type[c];
         if (t == CELL_SOLID) continue;
@@ -85,42 +90,53 @@ __global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs 
         s[6] = ff_add_f(s[6], u1);
         s[7] = ff_add_f(s[7], u2);
         umax = fmaxf(umax, sqrtf(u0 * u0 + u1 * u1 + u2 * u2));
-        const float dx = x - (float)O.cx, dy = y - (float)O.cy, dz = z - (float)O.cz;
+        const float dx = x - pcx, dy = y - pcy, dz = z - pcz;
         const float r2 = dx * dx + dy * dy + dz * dz;
-        const float pr = (ra + rb) * (1.0f / 3.0f) + (float)O.G * ra * rb;
-        if (r2 < (float)O.rin2) { s[8] = ff_add_f(s[8], pr); ++cin; }
-        if (r2 > (float)O.rout2) { s[9] = ff_add_f(s[9], pr); ++cout; }
+        const float pr = (ra + rb) * (1.0f / 3.0f) + Gf * ra * rb;
+        if (r2 < rin2) { s[8] = ff_add_f(s[8], pr); ++cin; }
+        if (r2 > rout2) { s[9] = ff_add_f(s[9], pr); ++cout; }
     }
-    double acc[NOBS];
+    // warp level in float-float and integers (FP32-rate work), then one FP64
+    // value per warp and slot; warp 0 sums the warps in FP64
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
-#pragma unroll
-    for (int k = 0; k < NS; ++k) acc[slot_of[k]] = (double)s[k].hi + (double)s[k].lo;
-    acc[8] = (double)umax;
-    acc[10] = (double)cin;
-    acc[12] = (double)cout;
-    acc[13] = (double)bad;
-    block_reduce(acc, sh);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < NOBS; ++k) partial[(size_t)blockIdx.x * NOBS + k] = acc[k];
+    for (int k = 0; k < NS; ++k) {
+        const ff v = warp_sum_ff(s[k]);
+        if (lane == 0) sh[slot_of[k] * 32 + warp] = (double)v.hi + (double)v.lo;
+    }
+    umax = warp_max_f(umax);
+    cin = warp_sum_i(cin);
+    cout = warp_sum_i(cout);
+    bad = warp_sum_i(bad);
+    if (lane == 0) {
+        sh[8 * 32 + warp] = (double)umax;
+        sh[10 * 32 + warp] = (double)cin;
+        sh[12 * 32 + warp] = (double)cout;
+        sh[13 * 32 + warp] = (double)bad;
+        sh[14 * 32 + warp] = 0.0;
+        sh[15 * 32 + warp] = 0.0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int k = 0; k < NOBS; ++k) {
+            double v = lane < nw ? sh[k * 32 + lane] : 0.0;
+            v = (k == SLOT_MAX) ? warp_max(v) : warp_sum(v);
+            if (lane == 0) partial[(size_t)blockIdx.x * NOBS + k] = v;
+        }
+    }
 }
 
-__global__ void __launch_bounds__(OBS_BLOCK) k_obs_final(const double *__restrict__ partial, int nblocks,
-                                                         double *__restrict__ out)
+__global__ void __launch_bounds__(OBS_FINAL_THREADS) k_obs_final(const double *__restrict__ partial, int nblocks,
+                                                                double *__restrict__ out)
 {
-    __shared__ double sh[NOBS * 32];
-    double acc[NOBS];
-#pragma unroll
-    for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < NOBS; ++k) {
-            const double v = partial[(size_t)b * NOBS + k];
-            acc[k] = (k == SLOT_MAX) ? fmax(acc[k], v) : acc[k] + v;
-        }
-    block_reduce(acc, sh);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < NOBS; ++k) out[k] = acc[k];
+    const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;  // warp k sums slot k
+    double v = 0.0;
+    for (int b = lane; b < nblocks; b += 32) {
+        const double x = partial[(size_t)b * NOBS + k];
+        v = (k == SLOT_MAX) ? fmax(v, x) : v + x;
+    }
+    v = (k == SLOT_MAX) ? warp_max(v) : warp_sum(v);
+    if (lane == 0) out[k] = v;
 }
 
 int obs_blocks(int n)
@@ -152,7 +168,7 @@ cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16, bool sync)
     k_obs_partial<<<nb, OBS_BLOCK, 0, ctx->stream>>>(ctx->dp, O, ctx->type, ctx->phi, ctx->macro, partial);
     prof_end(ctx, "k_obs_partial", e0);
     prof_begin(ctx, "k_obs_final", &e0);
-    k_obs_final<<<1, OBS_BLOCK, 0, ctx->stream>>>(partial, nb, out);
+    k_obs_final<<<1, OBS_FINAL_THREADS, 0, ctx->stream>>>(partial, nb, out);
     prof_end(ctx, "k_obs_final", e0);
     ctx->launches += 2;
     cudaError_t err = cudaGetLastError();

@@ -12,6 +12,7 @@ constexpr int NOBS = 16;
 constexpr int SLOT_MAX = 8;
 constexpr int OBS_BLOCK = 256;
 constexpr int OBS_MAX_BLOCKS = 608;
+constexpr int OBS_FINAL_THREADS = NOBS * 32;  // k_obs_final: one warp per slot
 
 struct ObsArgs {
     double cx, cy, cz, rin2, rout2, G;
@@ -22,8 +23,10 @@ struct ObsArgs {
 __global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs O, const uint8_t *__restrict__ type,
                               const float *__restrict__ phi, const float *__restrict__ macro,
                               double *__restrict__ partial);
-// One block: sums the nblocks rows of `partial` in a fixed order into out[NOBS].
-__global__ void __launch_bounds__(OBS_BLOCK) k_obs_final(const double *__restrict__ partial, int nblocks, double *__restrict__ out);
+// One block of OBS_FINAL_THREADS: sums the nblocks rows of `partial` in a fixed
+// order into out[NOBS].
+__global__ void __launch_bounds__(OBS_FINAL_THREADS) k_obs_final(const double *__restrict__ partial, int nblocks,
+                                                                double *__restrict__ out);
 
 int obs_blocks(int n);
 
