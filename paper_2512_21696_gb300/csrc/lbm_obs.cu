@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs 
     // the probe in FP32, converted once (a conversion from FP64 runs on the FP64 pipe)
     const float pcx = (float)O.cx, pcy = (float)O.cy, pcz = (float)O.cz;
     const float rin2 = (float)O.rin2, rout2 = (float)O.rout2, Gf = (float)O.G;
+    const bool probe = O.rin2 > 0.0 || O.rout2 < 3.0 * (double)n * (double)n;  // some cell can fall inside or outside
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         const uint8_t t = type[c];
         if (t == CELL_SOLID) continue;
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs 
             ++bad;
             continue;
         }
-        const int x = c % P.nx, y = (c / P.nx) % P.ny, z = c / (P.nx * P.ny);
+        const int x = c % P.nx;
         s[0] = ff_add_f(s[0], ra);
         s[1] = ff_add_f(s[1], rb);
         // saturation weight: phi in gray cells, 1 in pores, reservoirs left out
@@ -90,11 +91,14 @@ __global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs 
         s[6] = ff_add_f(s[6], u1);
         s[7] = ff_add_f(s[7], u2);
         umax = fmaxf(umax, sqrtf(u0 * u0 + u1 * u1 + u2 * u2));
-        const float dx = x - pcx, dy = y - pcy, dz = z - pcz;
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        const float pr = (ra + rb) * (1.0f / 3.0f) + Gf * ra * rb;
-        if (r2 < rin2) { s[8] = ff_add_f(s[8], pr); ++cin; }
-        if (r2 > rout2) { s[9] = ff_add_f(s[9], pr); ++cout; }
+        if (probe) {  // uniform: the pressure probe is set
+            const int xy = c / P.nx;
+            const float dx = x - pcx, dy = xy % P.ny - pcy, dz = xy / P.ny - pcz;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float pr = (ra + rb) * (1.0f / 3.0f) + Gf * ra * rb;
+            if (r2 < rin2) { s[8] = ff_add_f(s[8], pr); ++cin; }
+            if (r2 > rout2) { s[9] = ff_add_f(s[9], pr); ++cout; }
+        }
     }
     // warp level in float-float and integers (FP32-rate work), then one FP64
     // value per warp and slot; warp 0 sums the warps in FP64
