@@ -301,7 +301,9 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "frac_of_nominal_8tbs": round(achieved / 8000.0, 4),
-                     "traffic": ncu_traffic(dname),
+                     # the committed capture is of the F32 drainage launch
+                     "traffic": ncu_traffic(dname) if (args.storage == "f32" and args.workload == "drainage"
+                                                       and args.path == 0 and args.tile == 2) else None,
                      "alg_bytes_per_launch": alg.get(dkey, alg[step_key]),
                      "avg_launch_ms": round(avg_s * 1e3, 5)},
         "mflups": round(job_mlups(fluid, args.steps, world, ms), 2),  # non-solid cells only
