@@ -4,7 +4,7 @@
                 sources' rest populations (a local shift) in 16 bits.
 
 These are accuracy measurements of a storage format, not parity: each test
-prints the relative error of the quantity the variant is judged on
+prints the relative error of the quantity the variant is measured by
 (permeability along x/y/z in a tensorial fibre bundle, the Laplace pressure
 jump of a droplet, the mean saturation of a drainage run, mass) and bounds it
 by what the format delivers.  The F32 layout is measured alongside as the
