@@ -380,7 +380,10 @@ LBM_API int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int ckp
  * lbm_batch_create: runs[nruns] give each lattice's shape, body acceleration
  *   and probe; all other fields must be equal (LBM_ERR_ARG otherwise), and
  *   storage must be F32, F16R or BF16R.  Device buffers are owned by the
- *   batch.
+ *   batch.  The runs also share run 0's constitutive curves: set the same
+ *   curves on every run (lbm_batch_step and lbm_batch_tune return
+ *   LBM_ERR_STATE while they differ); reservoir densities and
+ *   mass-sink-source rates are per run.
  * lbm_batch_run: the context of one run, a view of the batch's buffers: use
  *   it with lbm_set_constitutive, lbm_set_geometry, lbm_init_fields,
  *   lbm_observables, lbm_get_fields, lbm_get_static and checkpoints (and

@@ -41,7 +41,7 @@ __device__ __forceinline__ float adj_phi_c(uint8_t t, float ph) { return t == CE
 
 // Pc / Pe of a curve at the clamped normalised saturation se and its
 // derivative in se: Brooks-Corey se^(-1/lambda); Thomeer
-// 2^min(k / log2(1 - se), log2 10) (derivative pw k / (log2(1 - se)^2 (1 - se))
+// 2^min(k / ln(1 - se), log2 10) (derivative pw ln2 k / (ln(1 - se)^2 (1 - se))
 // below the cap, 0 on it; 1 with derivative 0 at se = 1, where the clamp
 // stops the adjoint anyway).
 __device__ __forceinline__ float pc_shape(const Curve &cv, float se, float &dpw)
@@ -52,14 +52,14 @@ __device__ __forceinline__ float pc_shape(const Curve &cv, float se, float &dpw)
             dpw = 0.f;
             return 1.f;
         }
-        const float L = log2f(om);
+        const float L = log1pf(-se);
         const float E = cv.thomeer_k / L;
         if (E >= LOG2_10) {
             dpw = 0.f;
             return 10.f;
         }
         const float pw = exp2f(E);
-        dpw = pw * cv.thomeer_k / (L * L * om);
+        dpw = pw * 0.69314718f * cv.thomeer_k / (L * L * om);
         return pw;
     }
     const float pw = powf(se, cv.neg_inv_lambda);

@@ -102,8 +102,8 @@ void fill_device_params(lbm_ctx *ctx)
         d.curve[k].neg_inv_lambda = (float)(-1.0 / c.lambda);
         d.curve[k].nw = (float)c.nw;
         d.curve[k].nn = (float)c.nn;
-        // Thomeer: 10^(-G / ln(1 - Se)) = 2^(k / log2(1 - Se)), k = -G log2(10) / ln 2
-        d.curve[k].thomeer_k = c.thomeer_g > 0 ? (float)(-c.thomeer_g * std::log2(10.0) / std::log(2.0)) : 0.0f;
+        // Thomeer: 10^(-G / ln(1 - Se)) = 2^(k / ln(1 - Se)), k = -G log2(10)
+        d.curve[k].thomeer_k = c.thomeer_g > 0 ? (float)(-c.thomeer_g * std::log2(10.0)) : 0.0f;
     }
 }
 

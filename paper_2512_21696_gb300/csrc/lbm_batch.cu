@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <cstring>
 #include <new>
 #include <vector>
 
@@ -295,6 +296,10 @@ int slots_for(const lbm_batch *b, int tile, int *slots)
 // tables from device memory, so an upload needs no new capture.
 int sync_runs(lbm_batch *b)
 {
+    // the kernel reads the curve table of run 0 for every run
+    const lbm_ctx *v0 = b->views[0];
+    for (const auto *v : b->views)
+        if (std::memcmp(v->curves, v0->curves, sizeof(v0->curves)) != 0) return LBM_ERR_STATE;
     bool ext = false;
     for (auto *v : b->views) ext = ext || v->n_held > 0 || v->mss != 0.0;
     if (ext != b->ext) {

@@ -562,8 +562,9 @@ __device__ __forceinline__ void collide_store(const DevParams &P, const float (&
         if (H > 0.f) {
             const float se_c = fminf(fmaxf((sw - cv.swr) * cv.inv_1m_swr, 1e-2f), 1.f);
             // Pc / Pe: Brooks-Corey Se^(-1/lambda), or Thomeer
-            // 10^min(-G / ln(1 - Se), 1) = 2^min(k / log2(1 - Se), log2 10) (1 at Se = 1)
-            const float pw = cv.thomeer_k != 0.f ? exp2f(fminf(cv.thomeer_k / __log2f(1.f - se_c), LOG2_10))
+            // 10^min(-G / ln(1 - Se), 1) = 2^min(k / ln(1 - Se), log2 10) (1 at Se = 1); ln(1 - Se)
+            // by log1pf, accurate where Se is small and the quotient steep
+            const float pw = cv.thomeer_k != 0.f ? exp2f(fminf(cv.thomeer_k / log1pf(-se_c), LOG2_10))
                                                  : __powf(se_c, cv.neg_inv_lambda);
             const float Pc = gb.x * pw;
             const float k = __fdividef(-Pc * H, fmaxf(mag, P.eps_n)) * irt;

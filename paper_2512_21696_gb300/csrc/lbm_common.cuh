@@ -46,7 +46,7 @@ struct Curve {
     float inv_1m_swr;      // 1 / (1 - swr)
     float neg_inv_lambda;  // -1 / lambda
     float nw, nn;          // Corey exponents (wetting, non-wetting)
-    float thomeer_k;       // Thomeer Pc: -G log2(10) / ln 2; 0 selects Brooks-Corey
+    float thomeer_k;       // Thomeer Pc: -G log2(10); 0 selects Brooks-Corey
 };
 constexpr float LOG2_10 = 3.32192809488736234787f;
 

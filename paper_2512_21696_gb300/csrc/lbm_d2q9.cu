@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(256) k2_collide(DevParams P, const float *__re
         const float H = (fabsf(At_c) <= P.at_cut) ? 0.5f * mag : 0.f;
         if (H > 0.f) {  // capillary term of Eq. 1: -Pc(Sw) rho_r n H
             const float se_c = fminf(fmaxf((sw - cv.swr) * cv.inv_1m_swr, 1e-2f), 1.f);
-            const float pw = cv.thomeer_k != 0.f ? exp2f(fminf(cv.thomeer_k / __log2f(1.f - se_c), LOG2_10))
+            const float pw = cv.thomeer_k != 0.f ? exp2f(fminf(cv.thomeer_k / log1pf(-se_c), LOG2_10))
                                                  : __powf(se_c, cv.neg_inv_lambda);
             const float k = __fdividef(-gb.x * pw * H, fmaxf(mag, P.eps_n)) * irt;
             for (int d = 0; d < 2; ++d) {

@@ -177,3 +177,27 @@ def test_batch_steady_state_permeability_matches_oracle():
         ko = oobs["flux_vol"][0] * ((tau - 0.5) / 3.0) / g
         print(f"{case.name}: K gpu {kg:.6e} oracle {ko:.6e} after {steps} steps")
         assert ko > 0 and abs(kg - ko) <= 1e-4 * abs(ko)
+
+
+def test_batch_thomeer_runs_match_oracle():
+    """Runs on a Thomeer curve in a batch; the runs share run 0's curves, and
+    a run set to different curves stops the batch until they agree again."""
+    from paper_2512_21696_gb300 import lbm
+    cases = [LC.mixed_features(seed=41, thomeer=0.8), LC.mixed_features(shape=(7, 9, 6), seed=42, thomeer=0.8)]
+    b, views = _batch(cases)
+    try:
+        other = lbm.lbm_default_constitutive(thomeer_g=0.3)
+        lbm.lbm_set_constitutive(views[1], 1, other)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_batch_step(b, 2)
+        assert e.value.code == -6
+        _setup(views[1], cases[1])  # the same curves (and state) as run 0 again
+        lbm.lbm_batch_step(b, 10)
+        got = [[x.copy() for x in lbm.lbm_get_fields(v)] for v in views]
+    finally:
+        b.close()
+    for case, g in zip(cases, got):
+        of, _, _ = LC.run_oracle(case, 10)
+        fl = case.cell != synth.SOLID
+        for k, (x, y) in enumerate(zip(g, of)):
+            assert rel_l2(x, y, fl) <= 1e-5, (case.name, k)

@@ -103,3 +103,22 @@ def test_d2q9_is_refused_where_not_built():
         assert e.value.code == -1
     finally:
         ctx.close()
+
+
+def test_degenerate_planes():
+    """An all-solid plane steps and reports zero mass; a one-cell periodic
+    plane keeps its uniform state; a one-cell-wide channel with walls."""
+    from paper_2512_21696_gb300 import lbm
+    shape = (1, 6, 5)
+    solid = LC.Case("solid2d", shape, np.full(shape, synth.SOLID, np.uint8), np.ones(shape),
+                    np.full(shape, 0.5), np.full(shape, 0.5), lattice="d2q9", G=1.1)
+    _, gobs, _ = LC.run_gpu(solid, 3)
+    assert gobs["mass"] == (0.0, 0.0) and gobs["nan_count"] == 0
+    for shape, periodic in (((1, 1, 1), (1, 1, 1)), ((1, 7, 1), (1, 0, 1))):
+        rng = np.random.default_rng(3)
+        case = LC.Case(f"tiny2d{shape}", shape, np.zeros(shape, np.uint8), np.ones(shape),
+                       0.5 + 0.4 * rng.random(shape), 0.5 + 0.4 * rng.random(shape), lattice="d2q9", G=1.1,
+                       periodic=periodic, accel=((1e-4, 0, 0), (0, 0, 0)))
+        gf, _, _ = LC.run_gpu(case, 20)
+        of, _, _ = LC.run_oracle(case, 20)
+        _assert_parity(case, gf, of)

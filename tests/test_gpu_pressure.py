@@ -212,3 +212,15 @@ def test_pressure_levels_needs_reservoirs():
         assert ei.value.code == -6
     finally:
         ctx.close()
+
+
+def test_reservoirs_with_thomeer_curve_and_mass_source():
+    """Reservoir rows, a Thomeer pore type and a mass-sink-source rate at
+    once, on the fused path and the two launches."""
+    for path in (0, 1):
+        case = LC.imbibition(16)
+        case.curves = [dict(LC.CURVE, thomeer_g=0.4, aniso=5.0)]
+        case.s["mss"] = 1e-3
+        gf, _, _ = LC.run_gpu(case, 40, path=path)
+        of, _, _ = LC.run_oracle(case, 40)
+        _assert_parity(case, gf, of)
