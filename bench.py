@@ -186,6 +186,16 @@ def max_over_ranks(value, dist, device):
     return float(t.item())
 
 
+def sum_over_ranks(value, dist, device):
+    """Sum of a per-rank scalar (host-side reporting only)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def job_mlups(cells, steps, world, ms):
     """Whole-job throughput: every rank advances its own replica of `cells`."""
     return world * cells * steps / (ms * 1e-3) / 1e6
@@ -392,24 +402,40 @@ def run_reference(args, rank, world):
 REV_KINDS = ("spheres", "grf", "fibers", "slits")
 
 
-def rev_library(nruns, seed):
-    """Fully resolved REV runs: edge ~ U{24..64}, pore type round robin."""
+def rev_library(nruns, seed, first=0):
+    """Fully resolved REV runs first .. first + nruns - 1 of one seeded
+    library: edge ~ U{24..64}, pore type round robin (the same run index
+    gives the same REV whatever slice it is generated in)."""
     from paper_2512_21696_gb300 import synth
     rng = np.random.default_rng(seed)
-    edges = rng.integers(24, 65, size=nruns)
-    return [(int(e), REV_KINDS[r % 4]) + synth.rev_geometry(int(e), REV_KINDS[r % 4], seed + 1000 * (r + 1))[:2]
-            for r, e in enumerate(edges)]
+    edges = rng.integers(24, 65, size=first + nruns)
+    return [(int(edges[r]), REV_KINDS[r % 4]) + synth.rev_geometry(int(edges[r]), REV_KINDS[r % 4],
+                                                                   seed + 1000 * (r + 1))[:2]
+            for r in range(first, first + nruns)]
 
 
-def run_rev(args):
+def rev_slice(runs_per_rank, rank):
+    """The library runs of one rank: each rank advances its own runs_per_rank
+    REVs (weak scaling over independent problems, no data-path collective)."""
+    return rank * runs_per_rank, runs_per_rank
+
+
+def run_rev(args, rank=0, world=1, local_rank=0):
     """Single-phase permeability runs of a REV library (wetting B at rho_hi,
     A dissolved at rho_lo, g = 1e-4 on B along x, nu = 0.012): all runs in one
     batch (persistent launch per step, CUDA-graph replay, tuned tiles) against
-    the same runs stepped one after another."""
+    the same runs stepped one after another.  Under torchrun every rank runs
+    its own --rev-runs REVs of the library (weak scaling; the time is the
+    slowest rank's, the cells are summed)."""
     import torch
     from paper_2512_21696_gb300 import lbm, synth
-    torch.cuda.set_device(0)
-    lib = rev_library(args.rev_runs, synth.SEED_BASE + 5)
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    first, count = rev_slice(args.rev_runs, rank)
+    lib = rev_library(count, synth.SEED_BASE + 5, first)
     stream = torch.cuda.current_stream()
     tau = 3 * 0.012 + 0.5
     g = 1e-4
@@ -432,11 +458,14 @@ def run_rev(args):
     steps = args.steps + (args.steps & 1)
     lbm.lbm_batch_step(b, steps)  # captures the graph
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     ev0.record(stream)
     lbm.lbm_batch_step(b, steps)  # replays it
     ev1.record(stream)
     torch.cuda.synchronize()
-    ms_batch = ev0.elapsed_time(ev1)
+    ms_batch = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    cells_all = sum_over_ranks(sum(c.size for _, _, c, _ in lib), dist, "cuda")
     info = lbm.lbm_batch_info(b)
     # the same runs one after another (each its own single-lattice launches)
     ev0.record(stream)
@@ -444,7 +473,7 @@ def run_rev(args):
         lbm.lbm_step(v, steps)
     ev1.record(stream)
     torch.cuda.synchronize()
-    ms_seq = ev0.elapsed_time(ev1)
+    ms_seq = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     nu = (tau - 0.5) / 3.0
     kperm = {}
     taken = 0
@@ -465,15 +494,19 @@ def run_rev(args):
         steady = {"reached": bool(ok), "extra_steps": done, "wall_s": round(wall, 2),
                   "K": {k: round(float(np.mean(v)), 6) for k, v in ks.items()}}
     b.close()
-    mlups = cells * steps / (ms_batch * 1e-3) / 1e6
-    out = {"metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": 1, "steps": steps,
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    mlups = cells_all * steps / (ms_batch * 1e-3) / 1e6
+    out = {"metric": METRIC, "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world, "steps": steps,
            "warmup": args.warmup, "ms_per_step": ms_batch / steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded REV pore types)",
-           "config": {"workload": f"batched REV library: {len(lib)} single-phase runs, edge U{{24..64}}, "
+           "config": {"workload": f"batched REV library: {len(lib)} single-phase runs per GPU, edge U{{24..64}}, "
                                   "pore types spheres/grf/fibers/slits round robin",
-                      "storage": args.storage, "cells": cells, "fluid_frac": round(fluid / cells, 4),
-                      "l2": "inputs larger than L2"},
-           "sequential": {"value": round(cells * steps / (ms_seq * 1e-3) / 1e6, 2), "unit": "MLUPS",
+                      "storage": args.storage, "cells": int(cells_all), "fluid_frac": round(fluid / cells, 4),
+                      "parallelism": f"runs split x{world}", "l2": "inputs larger than L2"},
+           "sequential": {"value": round(cells_all * steps / (ms_seq * 1e-3) / 1e6, 2), "unit": "MLUPS",
                           "ms_per_step": ms_seq / steps},
            "batched_over_sequential": round(ms_seq / ms_batch, 3),
            "gpu_launches": info["groups"] * steps, "launches_per_step": info["groups"],
@@ -896,7 +929,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
     elif args.workload == "rev":
-        run_rev(args)
+        run_rev(args, rank, world, local_rank)
     elif args.workload == "adjoint":
         run_adjoint(args)
     elif args.workload == "droplet":

@@ -51,3 +51,23 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
     assert bench.job_mlups(100, 10, 1, 1.0) == pytest.approx(1.0)
+
+
+def test_rev_library_slices_are_disjoint_and_reproducible():
+    """Each rank of the REV workload advances its own runs of one seeded
+    library: the slices cover the library without overlap, and a run is the
+    same REV whichever slice generates it."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    world, per = 3, 2
+    slices = [bench.rev_slice(per, r) for r in range(world)]
+    covered = sorted(i for first, n in slices for i in range(first, first + n))
+    assert covered == list(range(world * per))
+    seed = 12345
+    whole = bench.rev_library(4, seed)
+    part = bench.rev_library(2, seed, first=2)
+    for (e1, k1, c1, p1), (e2, k2, c2, p2) in zip(whole[2:], part):
+        assert (e1, k1) == (e2, k2)
+        np.testing.assert_array_equal(c1, c2)
+        np.testing.assert_array_equal(p1, p2)
