@@ -58,10 +58,13 @@ def _from(f, c):
 
 
 def iso_grad(field):
-    """(1/cs^2) sum_i w_i field(x + c_i) c_i as [3, z, y, x]."""
+    """(1/cs^2) sum_i w_i field(x + c_i) c_i as [3, z, y, x]; summed as central
+    differences over the opposite pairs, so a flat field gives exactly 0."""
     comps = [torch.zeros_like(field) for _ in range(3)]
     for i in range(1, 19):
-        sh = _to(field, VEL[i])
+        if OPP[i] < i:
+            continue
+        sh = _to(field, VEL[i]) - _to(field, [-x for x in VEL[i]])
         for d in range(3):
             if VEL[i][d]:
                 comps[d] = comps[d] + WGT[i] * VEL[i][d] * sh / CS2

@@ -335,13 +335,16 @@ static void gray_static(orc_state *st, long c)
 {
     const orc_curve *cv = &st->curve[st->ptype[c]];
     double phi = st->phi[c];
-    /* gradient with the isotropic stencil of the lattice */
+    /* gradient with the isotropic stencil of the lattice, written as central
+     * differences over the opposite pairs (i < opp[i]): the same sum, and a
+     * flat neighbourhood gives exactly zero */
     const lattice *L = &st->L;
     double g[3] = {0, 0, 0};
-    for (int i = 0; i < L->Q; ++i) {
-        long m = neighbour(st, c, L->cv[i][0], L->cv[i][1], L->cv[i][2]);
-        double v = phi_seen(st, m);
-        for (int d = 0; d < 3; ++d) g[d] += L->w[i] * v * L->cv[i][d] / CS2;
+    for (int i = 1; i < L->Q; ++i) {
+        if (L->opp[i] < i) continue;
+        double vp = phi_seen(st, neighbour(st, c, L->cv[i][0], L->cv[i][1], L->cv[i][2]));
+        double vm = phi_seen(st, neighbour(st, c, -L->cv[i][0], -L->cv[i][1], -L->cv[i][2]));
+        for (int d = 0; d < 3; ++d) g[d] += L->w[i] * (vp - vm) * L->cv[i][d] / CS2;
     }
     /* Hessian: second differences on the faces, four-point cross terms */
     double H[3][3];

@@ -608,8 +608,9 @@ __global__ void k_geom_adjoint(DevParams P, CurveTableA T, double c_g, const uin
     if (lv2 == 0.0 || cv.aniso <= 1.0) return;
     const int x = c % P.nx, y = (c / P.nx) % P.ny, z = c / (P.nx * P.ny);
     double gr[3] = {0.0, 0.0, 0.0};
-    for (int i = 1; i < Q; ++i) {
-        const double v = phi_at(type, phi, nbr3(P, x, y, z, cx(i), cy(i), cz(i)));
+    for (int i = 1; i < Q; i += 2) {  // opposite pairs, as in the forward geometry
+        const double v = phi_at(type, phi, nbr3(P, x, y, z, cx(i), cy(i), cz(i))) -
+                         phi_at(type, phi, nbr3(P, x, y, z, -cx(i), -cy(i), -cz(i)));
         gr[0] += 3.0 * wgt_d(i) * cx(i) * v;
         gr[1] += 3.0 * wgt_d(i) * cy(i) * v;
         gr[2] += 3.0 * wgt_d(i) * cz(i) * v;

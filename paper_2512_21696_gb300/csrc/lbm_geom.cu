@@ -3,7 +3,8 @@
 //
 // Per gray cell (Eqs. 5-7 and the abstract's "Hessian and gradient of the
 // local porosity"):
-//   grad(phi)  isotropic D3Q19 stencil (1/cs^2) sum_i w_i phi(x+c_i) c_i;
+//   grad(phi)  isotropic D3Q19 stencil (1/cs^2) sum_i w_i phi(x+c_i) c_i,
+//              summed as central differences over opposite pairs;
 //   Hessian    second differences along the axes, four-point cross terms;
 //   M = H H + c_g grad(phi) grad(phi)^T; its top eigenvector e1 is the axis
 //   of lowest permeability, K = B diag(K0/a, K0, K0) B^T, so
@@ -102,9 +103,12 @@ __global__ void k_geometry(DevParams P, CurveTable T, double c_g, const uint8_t 
     if (type[c] != CELL_GRAY) return;
     const int x = c % P.nx, y = (c / P.nx) % P.ny, z = c / (P.nx * P.ny);
     const double ph = (double)phi[c];
+    // central differences over the opposite pairs (i odd, opp(i) = i + 1): a
+    // flat neighbourhood gives exactly zero, never round-off with an axis
     double g[3] = {0.0, 0.0, 0.0};
-    for (int i = 1; i < Q; ++i) {
-        const double v = phi_of(type, phi, nbr(P, x, y, z, cx(i), cy(i), cz(i)));
+    for (int i = 1; i < Q; i += 2) {
+        const double v = phi_of(type, phi, nbr(P, x, y, z, cx(i), cy(i), cz(i))) -
+                         phi_of(type, phi, nbr(P, x, y, z, -cx(i), -cy(i), -cz(i)));
         g[0] += 3.0 * wgt_d(i) * cx(i) * v;
         g[1] += 3.0 * wgt_d(i) * cy(i) * v;
         g[2] += 3.0 * wgt_d(i) * cz(i) * v;

@@ -267,3 +267,22 @@ def adjoint_case(n=8, seed=21, shape=None, steps_hint=None, thomeer=0.0):
     rb = 1.05 - ra
     return Case(f"adjoint{shape}", shape, cell, phi, ra, rb, curves=[dict(CURVE, aniso=10.0, thomeer_g=thomeer)], G=1.1,
                 kappa=-0.045, tau=(0.8, 1.0), accel=((1e-4, 0, 0), (0, 0, 0)), rho_wall=(0.03, 1.0), wet=1)
+
+
+def flat_blocks(lattice="d3q19", shape=None, periodic=(1, 1, 1), aniso=10.0, G=1.1, seed=2):
+    """Blocks of uniform porosity (gray phi 0.35 and 0.2) between open pore
+    and solid stripes: most gray cells see a flat neighbourhood (no axis),
+    the block faces have an axis normal to the face."""
+    shape = shape or ((1, 24, 30) if lattice == "d2q9" else (8, 16, 30))
+    nz, ny, nx = shape
+    x = np.arange(nx)[None, None, :]
+    y = np.arange(ny)[None, :, None]
+    cell = np.zeros(shape, np.uint8)
+    cell[...] = np.where((x % 15) >= 4, synth.GRAY, synth.PORE)
+    cell = np.where(((x % 15) == 14) & (y % 8 < 3), synth.SOLID, cell).astype(np.uint8)
+    phi = np.where(x < nx // 2, 0.35, 0.2) * np.ones(shape)
+    rng = np.random.default_rng(seed)
+    ra = np.where(x < nx // 3, 0.97, 0.03) * np.ones(shape) + 0.005 * rng.random(shape)
+    rb = 1.0 - ra + 0.005 * rng.random(shape)
+    return Case(f"flat_blocks_{lattice}{shape}", shape, cell, phi, ra, rb, lattice=lattice, periodic=periodic,
+                G=G, tau=(0.8, 1.0), accel=((1e-5, 0, 0), (0, 0, 0)), curves=[dict(CURVE, aniso=aniso)])

@@ -49,10 +49,13 @@ def shift_to(field, c):
 
 
 def iso_grad(field):
-    """(1/cs^2) sum_i w_i field(x + c_i) c_i, returned as [3][z][y][x]."""
+    """(1/cs^2) sum_i w_i field(x + c_i) c_i, returned as [3][z][y][x]; summed
+    as central differences over the opposite pairs, so a flat field gives 0."""
     out = np.zeros((3,) + field.shape, dtype=field.dtype)
     for i in range(1, 19):
-        sh = shift_to(field, VEL[i])
+        if OPP[i] < i:
+            continue
+        sh = shift_to(field, VEL[i]) - shift_to(field, -VEL[i])
         for d in range(3):
             if VEL[i][d]:
                 out[d] += WGT[i] * VEL[i][d] * sh / CS2

@@ -54,6 +54,23 @@ def test_mixed_features_small(steps, path, tile):
     _compare(case, gf, of)
 
 
+@pytest.mark.parametrize("lattice,periodic", [("d3q19", (1, 1, 1)), ("d3q19", (0, 1, 0)), ("d2q9", (1, 1, 1)),
+                                              ("d2q9", (0, 0, 1))])
+def test_flat_gray_blocks_static_and_step(lattice, periodic):
+    """Gray blocks of uniform porosity: the flat interiors carry no axis (an
+    exactly zero gradient and Hessian), the faces an axis along the normal;
+    the geometry precompute and 30 steps against the oracle."""
+    case = LC.flat_blocks(lattice, periodic=periodic)
+    gf, _, gst = LC.run_gpu(case, 30)
+    of, _, ost = LC.run_oracle(case, 30)
+    _compare_static(case, gst, ost)
+    inner = (case.cell == synth.GRAY) & (ost["iso"] == 1)
+    assert inner.sum() > 0.3 * (case.cell == synth.GRAY).sum()
+    for k in range(3, 6):  # no off-diagonal term where the oracle has no axis
+        assert np.all(gst[0][k][inner] == 0.0)
+    _compare(case, gf, of)
+
+
 @pytest.mark.parametrize("path,tile", [(0, 2), (1, 0)])
 def test_mixed_features_thomeer_curve(path, tile):
     """The second pore type on a Thomeer Pc curve (capillary force, residual

@@ -466,6 +466,62 @@ def test_laplace_law_two_dimensional(lattice):
 # --------------------------------------------------------------------------
 # Geometry precompute: Hessian axis, Leverett scaling, residual amounts
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("lattice", ["d3q19", "d2q9"])
+@pytest.mark.parametrize("phi0", [0.35, 0.1, 1 / 3, 0.7])
+def test_flat_porosity_has_no_axis(lattice, phi0):
+    """A region of uniform phi has zero gradient and Hessian (Eqs. 6-7), so M = 0
+    and no axis: K^-1 = I / K0 exactly, in a periodic block and in the interior
+    of a flat gray slab that borders open pore."""
+    shape = (1, 10, 12) if lattice == "d2q9" else (6, 10, 12)
+    aniso = 10.0
+    for slab in (False, True):
+        cell = np.full(shape, synth.GRAY, np.uint8)
+        if slab:
+            cell[..., :3] = synth.PORE
+        phi = np.where(cell == synth.GRAY, np.float32(phi0), 1.0).astype(np.float32).astype(np.float64)
+        o = O.Oracle(O.make_params(shape, lattice=lattice), cell, phi, curves=[O.make_curve(aniso=aniso)])
+        st = o.static()
+        gray = cell == synth.GRAY
+        # cells whose whole 3x3(x3) neighbourhood is gray with the same phi
+        inner = gray.copy()
+        if slab:
+            inner[..., :5] = False
+            inner[..., -1] = False  # periodic in x: its +x neighbour is pore
+        assert inner.any()
+        assert np.all(st["iso"][inner] == 1)
+        K0 = kc(float(np.float32(phi0)))
+        for idx in zip(*np.nonzero(inner)):
+            got = st["kinv"][(slice(None), slice(None)) + idx]
+            np.testing.assert_allclose(got, np.eye(3) / K0, rtol=1e-14)
+            assert np.all(got[~np.eye(3, dtype=bool)] == 0.0)
+        if slab:  # next to the pore the gradient is along x: the axis is x
+            edge = np.zeros(shape, bool)
+            edge[..., 3] = True
+            assert np.all(st["iso"][edge] == 0)
+            e = st["kinv"][0, 0][edge] * K0
+            np.testing.assert_allclose(e, aniso, rtol=1e-12)
+
+
+@pytest.mark.parametrize("delta", [1e-6, 1e-4])
+def test_tiny_porosity_wave_keeps_its_axis(delta):
+    """A real but tiny porosity variation phi0 + delta sin(2 pi x / n) has its
+    gradient and Hessian along x at every cell, so every cell is anisotropic
+    with e1 = x: the tie test's floor swallows round-off, not real gradients."""
+    n, aniso = 16, 5.0
+    shape = (4, 4, n)
+    x = np.arange(n)
+    phi = (0.35 + delta * np.sin(2 * np.pi * x / n))[None, None, :] * np.ones(shape)
+    phi = phi.astype(np.float32).astype(np.float64)
+    cell = np.full(shape, synth.GRAY, np.uint8)
+    st = O.Oracle(O.make_params(shape), cell, phi, curves=[O.make_curve(aniso=aniso)]).static()
+    assert np.all(st["iso"] == 0)
+    K0 = kc(phi)
+    np.testing.assert_allclose(st["kinv"][0, 0] * K0, aniso, rtol=1e-9)
+    np.testing.assert_allclose(st["kinv"][1, 1] * K0, 1.0, rtol=1e-9)
+    np.testing.assert_allclose(st["kinv"][2, 2] * K0, 1.0, rtol=1e-9)
+    assert np.abs(st["kinv"][0, 1] * K0).max() < 1e-9
+
+
 @pytest.mark.parametrize("m", [(1, 0, 0), (0, 1, 0), (1, 1, 0), (1, 1, 1), (1, 2, 3), (2, 0, 1)])
 def test_principal_axis_on_cosine_porosity(m):
     """Closed-form Hessian and gradient of phi0 + a cos(k.x), eigh for e1."""
