@@ -812,6 +812,76 @@ def run_imbibition2d(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------- 2-D fibre zigzag (D2Q9)
+def zigzag_pathway(nx=120, ny=180, half_width=10.0, amp=20.0, period=90.0):
+    """The open pathway of the Sec. I.B set-up on one plane: pore cells within
+    half_width (in x) of the sinusoidal centre line x_c(y) = nx/2 + amp
+    sin(2 pi y / period); the two fibre bundles on either side, out to the
+    walls, are gray."""
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    xc = nx / 2.0 - 0.5 + amp * np.sin(2.0 * np.pi * y / period)
+    return (np.abs(x - xc) <= half_width)[None]
+
+
+def run_zigzag2d(args):
+    """Single-phase flow through the zigzag pathway between two wavy-fibre
+    bundles (Sec. I.B, Sec. III.E) on D2Q9: the pathway is open pore
+    (phi = 1), the bundles gray with phi = 0.95; pressure rows on top and
+    bottom in the paper's ratio 0.740 : 0.733 (p = rho_B / 3, component B
+    alone: a dissolved A at rho_lo would bring the Eq. 1 drag of a component
+    whose relative permeability is floored at kr_min), walls left and right,
+    nu = 1.66e-2 (tau = 0.55), 120 x 180 cells between the pressure rows.
+    Isotropic resistivity from K0(phi) against the tensorial one whose least
+    component is 1e-4 K0 (Eq. 7).  Reports the fraction of the flux carried
+    inside the pathway (mean over the rows), both runs, and the step rate."""
+    import torch
+    from paper_2512_21696_gb300 import lbm, synth
+    torch.cuda.set_device(0)
+    nx, ny, lo, hi = 120, 180, 0.03, 1.0
+    path = zigzag_pathway(nx, ny)
+    cell = np.full((1, ny + 2, nx), synth.GRAY, np.uint8)
+    cell[0, 1:-1, :][path[0]] = synth.PORE
+    cell[0, -1, :], cell[0, 0, :] = synth.INLET, synth.OUTLET
+    phi_all = np.where(cell == synth.GRAY, 0.95, 1.0).astype(np.float32)
+    rho_in = hi * 0.740 / 0.733
+    stream = torch.cuda.current_stream()
+    res, total_ms = {}, 0.0
+    for aniso in (1.0, 1e4):
+        p = lbm.lbm_default_params(nx, ny + 2, 1, stream=stream.cuda_stream, G=1.1, tau=(0.55, 0.55),
+                                   rho_wall=(lo, hi), wet_idx=1, periodic=(0, 0, 1), lattice=1)
+        ctx = lbm.lbm_create(p)
+        lbm.lbm_set_constitutive(ctx, 0, lbm.lbm_default_constitutive(aniso=aniso))
+        lbm.lbm_set_geometry(ctx, cell, phi_all)
+        lbm.lbm_init_fields(ctx, np.zeros(cell.shape, np.float32), np.full(cell.shape, hi, np.float32))
+        lbm.lbm_set_pressure(ctx, (0.0, rho_in), (0.0, hi))
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lbm.lbm_step(ctx, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        obs = lbm.lbm_observables(ctx, check=False)
+        a, b, u, sw = lbm.lbm_get_fields(ctx)
+        ctx.close()
+        uy = -u[1, 0, 1:-1, :]  # flow runs from the top row down
+        inside = (uy * path[0]).sum(axis=1) / uy.sum(axis=1)
+        res["tensorial" if aniso > 1 else "isotropic"] = {
+            "pathway_flux_fraction": round(float(inside.mean()), 4),
+            "pathway_width_fraction": round(float(path.mean()), 4),
+            "flux_per_row": float(uy.sum(axis=1).mean()), "nan_count": obs["nan_count"]}
+    cells = nx * (ny + 2)
+    out = {"metric": METRIC, "value": round(cells * 2 * args.steps / (total_ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+           "n_gpus": 1, "steps": 2 * args.steps, "warmup": 0, "ms_per_step": total_ms / (2 * args.steps),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (zigzag pathway between gray fibre bundles)",
+           "config": {"workload": "Sec. I.B / III.E zigzag pathway on D2Q9: 120 x 180, open pathway between "
+                                  "phi = 0.95 fibre bundles, pressure rows, isotropic vs tensorial resistivity",
+                      "cells": cells},
+           "gpu_launches": 2 * 2 * args.steps, "zigzag": res}
+    print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------ static droplet
 def run_droplet(args):
     """32^3 static droplet (R = 8, rho 1.0/0.03, G = 1.1, tau = 1): the state
@@ -915,7 +985,7 @@ def main():
     ap.add_argument("--storage", choices=list(STORAGE_IDS), default="f32",
                     help="population storage: f32; f16 / bf16 globally shifted; f16r / bf16r rest-referenced (FP32 arithmetic)")
     ap.add_argument("--workload", choices=("drainage", "fiber", "droplet", "rev", "revlib", "adjoint", "imbibition",
-                                           "droplet2d", "imbibition2d"),
+                                           "droplet2d", "imbibition2d", "zigzag2d"),
                     default="drainage",
                     help="drainage: the 128^3 multiscale-rock step; fiber: the 192^3 tensorial fibre bundle; "
                          "droplet: the 32^3 static droplet (CUDA-graph replay); rev: the batched REV library; "
@@ -923,7 +993,8 @@ def main():
                          "adjoint: the porosity gradient on the 96^3 recipe; "
                          "imbibition: the stepped-pressure Pc-Sw protocol between reservoir planes; "
                          "droplet2d: the Sec. III.A droplet on D2Q9; "
-                         "imbibition2d: the Sec. III.B random-porosity imbibition on D2Q9")
+                         "imbibition2d: the Sec. III.B random-porosity imbibition on D2Q9; "
+                         "zigzag2d: the zigzag pathway between fibre bundles of Sec. I.B / III.E on D2Q9")
     ap.add_argument("--level-max", type=int, default=10000, help="imbibition: most steps per pressure level")
     ap.add_argument("--ckpt", type=int, default=100, help="adjoint checkpoint interval")
     ap.add_argument("--rev-runs", type=int, default=256)
@@ -955,6 +1026,8 @@ def main():
         run_droplet2d(args)
     elif args.workload == "imbibition2d":
         run_imbibition2d(args)
+    elif args.workload == "zigzag2d":
+        run_zigzag2d(args)
     else:
         run_ours(args, rank, world, local_rank)
 
