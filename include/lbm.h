@@ -232,7 +232,15 @@ LBM_API int lbm_set_geometry(lbm_ctx *ctx, const uint8_t *type, const float *phi
 LBM_API int lbm_init_fields(lbm_ctx *ctx, const float *rhoA, const float *rhoB, const float *u, int mem);
 
 /* Advance nsteps >= 0 time steps (asynchronous).  The fields read back by
- * lbm_get_fields / lbm_observables are those of the last step. */
+ * lbm_get_fields / lbm_observables are those of the last step.  On lattices
+ * of at most 2^18 cells (not batch runs, not while profiling) a call of more
+ * than 33 steps replays CUDA graphs of 32 steps, captured on first use per
+ * buffer parity and dropped by every call that changes a parameter
+ * (lbm_set_constitutive, lbm_set_geometry, lbm_set_pressure, lbm_set_mss,
+ * lbm_init_fields, lbm_load_state, lbm_set_kernel, lbm_profile); the
+ * replayed kernels are the same launches, so the result is bit-identical and
+ * lbm_launch_count counts them.  A failed capture falls back to direct
+ * launches for the rest of the context's life. */
 LBM_API int lbm_step(lbm_ctx *ctx, int nsteps);
 
 /* Pressure boundaries: the densities held in the LBM_CELL_INLET and

@@ -10,6 +10,16 @@
 #include "lbm_context.h"
 #include "lbm_host.h"
 
+namespace lbm {
+void drop_graphs(lbm_ctx *ctx)
+{
+    for (auto &gx : ctx->graph) {
+        if (gx) cudaGraphExecDestroy(gx);
+        gx = nullptr;
+    }
+}
+}  // namespace lbm
+
 namespace lbm_host {
 
 thread_local char g_last_cuda_error[256] = "";
@@ -52,6 +62,7 @@ size_t pop_bytes(const lbm_ctx *ctx)
 
 void fill_device_params(lbm_ctx *ctx)
 {
+    lbm::drop_graphs(ctx);  // the kernels take these parameters by value
     const lbm_params &p = ctx->p;
     lbm::DevParams &d = ctx->dp;
     d.nx = p.nx;
@@ -305,6 +316,8 @@ int lbm_destroy(lbm_ctx *ctx)
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
+    lbm::drop_graphs(ctx);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
     cudaFree(ctx->f[0]);
     cudaFree(ctx->f[1]);
     cudaFree(ctx->type);
@@ -479,6 +492,7 @@ int lbm_init_fields(lbm_ctx *ctx, const float *rhoA, const float *rhoB, const fl
     if ((rc = stage_in(rhoA, N * sizeof(float), mem, ctx->stream, sa, &da)) != LBM_OK) return rc;
     if ((rc = stage_in(rhoB, N * sizeof(float), mem, ctx->stream, sb, &db)) != LBM_OK) return rc;
     if (u && (rc = stage_in(u, 3 * N * sizeof(float), mem, ctx->stream, su, &du)) != LBM_OK) return rc;
+    lbm::drop_graphs(ctx);
     ctx->cur = 0;
     if (ctx->p.lattice == LBM_LATTICE_D2Q9)
         LBM_CUDA(lbm::launch_d2q9_init(ctx, (const float *)da, (const float *)db, (const float *)du));
@@ -490,25 +504,88 @@ int lbm_init_fields(lbm_ctx *ctx, const float *rhoA, const float *rhoB, const fl
     return LBM_OK;
 }
 
+// One step: its kernels on ctx->stream (fields written if write_macro).
+static cudaError_t step_once(lbm_ctx *ctx, bool write_macro)
+{
+    cudaError_t e;
+    if (ctx->p.lattice == LBM_LATTICE_D2Q9) {
+        e = lbm::launch_d2q9_step(ctx, write_macro);
+    } else if (ctx->p.storage == LBM_STORAGE_F16S || ctx->p.storage == LBM_STORAGE_BF16S) {
+        e = lbm::launch_fused_lp(ctx, write_macro);
+    } else if (ctx->path == 1 && ctx->p.storage == LBM_STORAGE_F32) {
+        e = lbm::launch_density(ctx);
+        if (e == cudaSuccess) e = lbm::launch_collide(ctx, write_macro);
+    } else {
+        e = lbm::launch_fused(ctx, write_macro);
+    }
+    if (e == cudaSuccess) ctx->steps += 1;
+    return e;
+}
+
+// Captures GRAPH_STEPS steps (no field output) from the current buffer parity
+// on the private stream; nothing runs.  Returns false, with the context as
+// before, when the capture or instantiation fails.
+static bool capture_steps(lbm_ctx *ctx)
+{
+    if (!ctx->cap && cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const cudaStream_t user = ctx->stream;
+    const int cur0 = ctx->cur;
+    const long long steps0 = ctx->steps, launches0 = ctx->launches;
+    ctx->stream = ctx->cap;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int k = 0; k < lbm::GRAPH_STEPS && e == cudaSuccess; ++k) e = step_once(ctx, false);
+        const cudaError_t ce = cudaStreamEndCapture(ctx->cap, &graph);
+        if (e == cudaSuccess) e = ce;
+    }
+    ctx->stream = user;
+    const long long per_replay = ctx->launches - launches0;
+    ctx->cur = cur0;  // nothing ran: the state is where it was
+    ctx->steps = steps0;
+    ctx->launches = launches0;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // capture errors leave the context usable
+        return false;
+    }
+    ctx->graph[cur0] = exec;
+    ctx->graph_launches = per_replay;
+    return true;
+}
+
 int lbm_step(lbm_ctx *ctx, int nsteps)
 {
     if (!ctx || nsteps < 0) return LBM_ERR_ARG;
     if (!ctx->has_fields) return LBM_ERR_STATE;
     DeviceGuard g(ctx->dev);
     if (!g.ok) return LBM_ERR_CUDA;
-    for (int k = 0; k < nsteps; ++k) {
-        if (ctx->p.lattice == LBM_LATTICE_D2Q9) {
-            LBM_CUDA(lbm::launch_d2q9_step(ctx, k == nsteps - 1));
-        } else if (ctx->p.storage == LBM_STORAGE_F16S || ctx->p.storage == LBM_STORAGE_BF16S) {
-            LBM_CUDA(lbm::launch_fused_lp(ctx, k == nsteps - 1));
-        } else if (ctx->path == 1 && ctx->p.storage == LBM_STORAGE_F32) {
-            LBM_CUDA(lbm::launch_density(ctx));
-            LBM_CUDA(lbm::launch_collide(ctx, k == nsteps - 1));
-        } else {
-            LBM_CUDA(lbm::launch_fused(ctx, k == nsteps - 1));
+    int k = 0;
+    // small lattices: after one direct step (which also resolves each
+    // kernel's launch configuration), replay GRAPH_STEPS-step graphs while
+    // more than GRAPH_STEPS steps remain; the last steps, which write the
+    // fields, run directly
+    if (!ctx->view && !ctx->profiling && !ctx->graph_off && ctx->n <= lbm::GRAPH_MAX_CELLS &&
+        nsteps > lbm::GRAPH_STEPS + 1) {
+        LBM_CUDA(step_once(ctx, false));
+        k = 1;
+        while (nsteps - k > lbm::GRAPH_STEPS) {
+            if (!ctx->graph[ctx->cur] && !capture_steps(ctx)) {
+                ctx->graph_off = true;
+                break;
+            }
+            LBM_CUDA(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
+            ctx->steps += lbm::GRAPH_STEPS;
+            ctx->launches += ctx->graph_launches;
+            k += lbm::GRAPH_STEPS;  // even: the state is back in buffer cur
         }
-        ctx->steps += 1;
     }
+    for (; k < nsteps; ++k) LBM_CUDA(step_once(ctx, k == nsteps - 1));
     return LBM_OK;
 }
 
@@ -640,6 +717,7 @@ int lbm_load_state(lbm_ctx *ctx, const void *buf, size_t bytes)
     if (!g.ok) return LBM_ERR_CUDA;
     const size_t N = (size_t)ctx->n;
     const char *p = (const char *)buf + 4 * sizeof(long long);
+    lbm::drop_graphs(ctx);
     ctx->cur = 0;
     LBM_CUDA(cudaMemcpyAsync(ctx->f[0], p, pop_bytes(ctx), cudaMemcpyHostToDevice, ctx->stream));
     p += pop_bytes(ctx);
@@ -662,6 +740,7 @@ int lbm_profile(lbm_ctx *ctx, int enable)
     }
     ctx->prof.clear();
     ctx->profiling = enable != 0;
+    lbm::drop_graphs(ctx);
     return LBM_OK;
 }
 
@@ -697,6 +776,7 @@ int lbm_set_kernel(lbm_ctx *ctx, int path, int tile)
     if (!ctx || path < 0 || path > 1 || tile < 0 || tile > 4) return LBM_ERR_ARG;
     ctx->path = path;
     ctx->tile = tile;
+    lbm::drop_graphs(ctx);
     return LBM_OK;
 }
 

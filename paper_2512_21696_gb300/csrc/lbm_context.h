@@ -42,6 +42,15 @@ struct lbm_ctx {
     long long steps = 0;
     long long launches = 0;
 
+    // CUDA-graph replay of runs of steps on small lattices (launch-bound):
+    // one executable graph per buffer parity, each GRAPH_STEPS steps without
+    // field output; dropped whenever a parameter the kernels take by value
+    // changes
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long graph_launches = 0;  // kernel launches one replay stands for
+    cudaStream_t cap = nullptr;    // private capture stream
+    bool graph_off = false;        // a capture failed: step directly from then on
+
     struct ProfRec {
         const char *name;
         cudaEvent_t a, b;
@@ -59,6 +68,14 @@ constexpr int NOBS_HOST = 16;
 
 // A run of the batch changed a per-run parameter: its next step re-reads the runs.
 void batch_runs_changed(struct lbm_batch *b);
+
+// Steps per replayed graph (even: the replay returns to the same buffer) and
+// the largest lattice that replays graphs (above it a step is long enough to
+// hide its launch).
+constexpr int GRAPH_STEPS = 32;
+constexpr int GRAPH_MAX_CELLS = 1 << 18;
+// Frees the context's step graphs (the next lbm_step captures new ones).
+void drop_graphs(lbm_ctx *ctx);
 
 // Kernel launches (each records itself in ctx->launches and, while profiling,
 // brackets the launch with CUDA events).
