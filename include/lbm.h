@@ -149,7 +149,8 @@ typedef struct lbm_constitutive {
     double thomeer_g; /* Thomeer pore-geometrical factor G > 0, or 0 for Brooks-Corey */
 } lbm_constitutive;
 
-/* Observables of the current fields (FP64 reductions). */
+/* Observables of the current fields: deterministic float-float sums (about
+ * 48 bits, counts exact), reported in FP64. */
 typedef struct lbm_obs {
     double mass[2];      /* sum of rho^a over non-solid cells */
     double sat;          /* sum(phi_c Sw)/sum(phi_c); phi_c = 1 pore, phi gray */
@@ -303,7 +304,7 @@ LBM_API int lbm_mss_to_saturation(lbm_ctx *ctx, double target, double gain, doub
 LBM_API int lbm_pressure_levels(lbm_ctx *ctx, int nlevels, const double *rho_in, const double *rho_out,
                                 int check_every, double sat_tol, int max_steps, double *sat, int *steps);
 
-/* FP64 reductions of the current fields into *out (synchronises).
+/* Reductions of the current fields into *out (synchronises).
  * Returns LBM_ERR_NUMERIC when nan_count > 0 (out is still filled). */
 LBM_API int lbm_observables(lbm_ctx *ctx, lbm_obs *out);
 

@@ -65,15 +65,9 @@ extern "C" LBM_API int lbm_observables_noalloc(const float *fields, const uint8_
     P.ny = ny;
     P.nz = nz;
     P.n = (int)n;
-    lbm::ObsArgs O;
-    O.cx = probe[0];
-    O.cy = probe[1];
-    O.cz = probe[2];
-    O.rin2 = probe[3] * probe[3];
-    O.rout2 = probe[4] * probe[4];
-    O.G = G;
+    const lbm::ObsArgs O = lbm::obs_args(probe, probe[3], probe[4], G, n);
     const int nb = lbm::obs_blocks((int)n);
-    double *partial = scratch;
+    float2 *partial = reinterpret_cast<float2 *>(scratch);  // a float-float pair per double slot
     double *final_row = scratch + (size_t)lbm::OBS_MAX_BLOCKS * lbm::NOBS;
     cudaStream_t s = (cudaStream_t)stream;
     lbm::k_obs_partial<<<nb, lbm::OBS_BLOCK, 0, s>>>(P, O, type, phi, fields, partial);

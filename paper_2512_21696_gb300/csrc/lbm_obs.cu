@@ -1,15 +1,17 @@
-// Observables of the current fields (FP64 reductions) and read-back of the
-// gray-cell geometry results.
+// Observables of the current fields (float-float reductions, FP64 results)
+// and read-back of the gray-cell geometry results.
 //
-// k_obs_partial: grid-stride pass, per-thread float-float accumulators
+// k_obs_partial: grid-stride pass (two cells' loads in flight per thread),
+//                per-thread float-float accumulators
 //                (error-free FP32 sums, about 48 bits: FP64 arithmetic runs at
-//                a small fraction of the FP32 rate on this part), converted
-//                to FP64 once per thread for the warp-shuffle and
-//                shared-memory block reduction, one row of partials per block
-//                in the reduction scratch;
+//                a small fraction of the FP32 rate on this part), float-float
+//                warp-shuffle and shared-memory block reduction, one row of
+//                float-float partials per block in the reduction scratch (a
+//                pair in each double slot);
 // k_obs_final:   one block, one warp per slot: each lane sums a fixed
 //                subset of the rows, then the warp combines the lanes in a
-//                fixed order (deterministic), in FP64.
+//                fixed order (deterministic), in float-float; each slot's
+//                result is converted to FP64 once.
 #include <cfloat>
 
 #include "lbm_context.h"
@@ -17,16 +19,6 @@
 
 namespace lbm {
 
-__device__ __forceinline__ double warp_sum(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_max(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    return v;
-}
 
 // float-float sum over the warp (lane 0 gets it)
 __device__ __forceinline__ ff warp_sum_ff(ff v)
@@ -48,13 +40,13 @@ __device__ __forceinline__ float warp_max_f(float v)
     return v;
 }
 
-__global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs O,
+__global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsArgs O,
                                                            const uint8_t *__restrict__ type,
                                                            const float *__restrict__ phi,
                                                            const float *__restrict__ macro,
-                                                           double *__restrict__ partial)
+                                                           float2 *__restrict__ partial)
 {
-    __shared__ double sh[NOBS * 32];
+    __shared__ float2 sh[NOBS * 32];
     // slots 0-7, 9, 11 summed in float-float; 10, 12, 13 are counts
     constexpr int NS = 10;
     constexpr int slot_of[NS] = {0, 1, 2, 3, 4, 5, 6, 7, 9, 11};
@@ -64,83 +56,109 @@ __global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs 
     int cin = 0, cout = 0, bad = 0;
     const int n = P.n;
     float umax = 0.0f;
-    // the probe in FP32, converted once (a conversion from FP64 runs on the FP64 pipe)
-    const float pcx = (float)O.cx, pcy = (float)O.cy, pcz = (float)O.cz;
-    const float rin2 = (float)O.rin2, rout2 = (float)O.rout2, Gf = (float)O.G;
-    const bool probe = O.rin2 > 0.0 || O.rout2 < 3.0 * (double)n * (double)n;  // some cell can fall inside or outside
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        const uint8_t t = type[c];
-        if (t == CELL_SOLID) continue;
-        // per-cell terms in FP32 (products of FP32 fields, one rounding each)
-        const float ra = macro[c], rb = macro[(size_t)n + c];
-        const float u0 = macro[(size_t)2 * n + c], u1 = macro[(size_t)3 * n + c], u2 = macro[(size_t)4 * n + c];
-        const float sw = macro[(size_t)5 * n + c];
-        if (!isfinite(ra) || !isfinite(rb) || !isfinite(u0) || !isfinite(u1) || !isfinite(u2)) {
-            ++bad;
-            continue;
+    const float pcx = O.cx, pcy = O.cy, pcz = O.cz, rin2 = O.rin2, rout2 = O.rout2, Gf = O.G;
+    const bool probe = O.probe != 0;  // some cell can fall inside or outside
+    // cells c0 + k stride, k < UNR, per pass: all their loads are issued before
+    // any is used (the fields of solid cells are read and ignored), so a pass
+    // waits on memory once; the cells are summed in the grid-stride order
+    constexpr int UNR = 2;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; c0 < n; c0 += UNR * stride) {
+        uint8_t tk[UNR];
+        float fk[UNR][7];
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+            const long long ck = c0 + k * stride;
+            tk[k] = CELL_SOLID;
+            if (ck < n) {
+                tk[k] = type[ck];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) fk[k][q] = macro[(size_t)q * n + ck];
+                fk[k][6] = phi[ck];
+            }
         }
-        const int x = c % P.nx;
-        s[0] = ff_add_f(s[0], ra);
-        s[1] = ff_add_f(s[1], rb);
-        // saturation weight: phi in gray cells, 1 in pores, reservoirs left out
-        const float phc = t == CELL_GRAY ? phi[c] : (t == CELL_PORE ? 1.0f : 0.0f);
-        s[2] = ff_add_f(s[2], phc * sw);
-        s[3] = ff_add_f(s[3], phc);
-        if (x == P.nx - 1) s[4] = ff_add_f(s[4], u0);
-        s[5] = ff_add_f(s[5], u0);
-        s[6] = ff_add_f(s[6], u1);
-        s[7] = ff_add_f(s[7], u2);
-        umax = fmaxf(umax, sqrtf(u0 * u0 + u1 * u1 + u2 * u2));
-        if (probe) {  // uniform: the pressure probe is set
-            const int xy = c / P.nx;
-            const float dx = x - pcx, dy = xy % P.ny - pcy, dz = xy / P.ny - pcz;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            const float pr = (ra + rb) * (1.0f / 3.0f) + Gf * ra * rb;
-            if (r2 < rin2) { s[8] = ff_add_f(s[8], pr); ++cin; }
-            if (r2 > rout2) { s[9] = ff_add_f(s[9], pr); ++cout; }
+#pragma unroll
+        for (int k = 0; k < UNR; ++k) {
+            const uint8_t t = tk[k];
+            if (t == CELL_SOLID) continue;
+            const int c = (int)(c0 + k * stride);
+            // per-cell terms in FP32 (products of FP32 fields, one rounding each)
+            const float ra = fk[k][0], rb = fk[k][1];
+            const float u0 = fk[k][2], u1 = fk[k][3], u2 = fk[k][4];
+            const float sw = fk[k][5];
+            if (!isfinite(ra) || !isfinite(rb) || !isfinite(u0) || !isfinite(u1) || !isfinite(u2)) {
+                ++bad;
+                continue;
+            }
+            const int x = c % P.nx;
+            s[0] = ff_add_f(s[0], ra);
+            s[1] = ff_add_f(s[1], rb);
+            // saturation weight: phi in gray cells, 1 in pores, reservoirs left out
+            const float phc = t == CELL_GRAY ? fk[k][6] : (t == CELL_PORE ? 1.0f : 0.0f);
+            s[2] = ff_add_f(s[2], phc * sw);
+            s[3] = ff_add_f(s[3], phc);
+            if (x == P.nx - 1) s[4] = ff_add_f(s[4], u0);
+            s[5] = ff_add_f(s[5], u0);
+            s[6] = ff_add_f(s[6], u1);
+            s[7] = ff_add_f(s[7], u2);
+            umax = fmaxf(umax, sqrtf(u0 * u0 + u1 * u1 + u2 * u2));
+            if (probe) {  // uniform: the pressure probe is set
+                const int xy = c / P.nx;
+                const float dx = x - pcx, dy = xy % P.ny - pcy, dz = xy / P.ny - pcz;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float pr = (ra + rb) * (1.0f / 3.0f) + Gf * ra * rb;
+                if (r2 < rin2) { s[8] = ff_add_f(s[8], pr); ++cin; }
+                if (r2 > rout2) { s[9] = ff_add_f(s[9], pr); ++cout; }
+            }
         }
     }
-    // warp level in float-float and integers (FP32-rate work), then one FP64
-    // value per warp and slot; warp 0 sums the warps in FP64
+    // warp and block levels in float-float and integers, all on the FP32
+    // pipe (a few FP64 operations per block, times 608 blocks, had kept the
+    // FP64 pipe a third busy); counts stay exact as float-float
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
         const ff v = warp_sum_ff(s[k]);
-        if (lane == 0) sh[slot_of[k] * 32 + warp] = (double)v.hi + (double)v.lo;
+        if (lane == 0) sh[slot_of[k] * 32 + warp] = make_float2(v.hi, v.lo);
     }
     umax = warp_max_f(umax);
     cin = warp_sum_i(cin);
     cout = warp_sum_i(cout);
     bad = warp_sum_i(bad);
     if (lane == 0) {
-        sh[8 * 32 + warp] = (double)umax;
-        sh[10 * 32 + warp] = (double)cin;
-        sh[12 * 32 + warp] = (double)cout;
-        sh[13 * 32 + warp] = (double)bad;
-        sh[14 * 32 + warp] = 0.0;
-        sh[15 * 32 + warp] = 0.0;
+        sh[8 * 32 + warp] = make_float2(umax, 0.f);
+        sh[10 * 32 + warp] = make_float2((float)cin, 0.f);  // a warp counts far fewer than 2^24 cells: exact
+        sh[12 * 32 + warp] = make_float2((float)cout, 0.f);
+        sh[13 * 32 + warp] = make_float2((float)bad, 0.f);
+        sh[14 * 32 + warp] = make_float2(0.f, 0.f);
+        sh[15 * 32 + warp] = make_float2(0.f, 0.f);
     }
     __syncthreads();
     if (warp == 0) {
         for (int k = 0; k < NOBS; ++k) {
-            double v = lane < nw ? sh[k * 32 + lane] : 0.0;
-            v = (k == SLOT_MAX) ? warp_max(v) : warp_sum(v);
-            if (lane == 0) partial[(size_t)blockIdx.x * NOBS + k] = v;
+            const float2 x = lane < nw ? sh[k * 32 + lane] : make_float2(0.f, 0.f);
+            ff v = {x.x, x.y};
+            if (k == SLOT_MAX) v.hi = warp_max_f(v.hi);
+            else v = warp_sum_ff(v);
+            if (lane == 0) partial[(size_t)blockIdx.x * NOBS + k] = make_float2(v.hi, v.lo);
         }
     }
 }
 
-__global__ void __launch_bounds__(OBS_FINAL_THREADS) k_obs_final(const double *__restrict__ partial, int nblocks,
+__global__ void __launch_bounds__(OBS_FINAL_THREADS) k_obs_final(const float2 *__restrict__ partial, int nblocks,
                                                                 double *__restrict__ out)
 {
     const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;  // warp k sums slot k
-    double v = 0.0;
-    for (int b = lane; b < nblocks; b += 32) {
-        const double x = partial[(size_t)b * NOBS + k];
-        v = (k == SLOT_MAX) ? fmax(v, x) : v + x;
+    ff v = {0.f, 0.f};
+#pragma unroll 8
+    for (int b = lane; b < nblocks; b += 32) {  // unrolled: the loads go out together
+        const float2 x = partial[(size_t)b * NOBS + k];
+        if (k == SLOT_MAX) v.hi = fmaxf(v.hi, x.x);
+        else v = ff_add(v, ff{x.x, x.y});
     }
-    v = (k == SLOT_MAX) ? warp_max(v) : warp_sum(v);
-    if (lane == 0) out[k] = v;
+    if (k == SLOT_MAX) v.hi = warp_max_f(v.hi);
+    else v = warp_sum_ff(v);
+    if (lane == 0) out[k] = (double)v.hi + (double)v.lo;
 }
 
 int obs_blocks(int n)
@@ -157,15 +175,9 @@ cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16) { return launch
 cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16, bool sync)
 {
     const lbm_params &p = ctx->p;
-    ObsArgs O;
-    O.cx = p.probe_center[0];
-    O.cy = p.probe_center[1];
-    O.cz = p.probe_center[2];
-    O.rin2 = p.probe_r_in * p.probe_r_in;
-    O.rout2 = p.probe_r_out * p.probe_r_out;
-    O.G = p.G;
+    const ObsArgs O = obs_args(p.probe_center, p.probe_r_in, p.probe_r_out, p.G, ctx->n);
     const int nb = obs_blocks(ctx->n);
-    double *partial = ctx->red;
+    float2 *partial = reinterpret_cast<float2 *>(ctx->red);  // a float-float pair per double slot
     double *out = ctx->red + (size_t)nb * NOBS;
     cudaEvent_t e0;
     prof_begin(ctx, "k_obs_partial", &e0);

@@ -1,5 +1,8 @@
-// Shared declarations of the FP64 observable reduction (lbm_obs.cu).
+// Shared declarations of the observable reduction (lbm_obs.cu): float-float
+// sums on the FP32 pipe, FP64 results.
 #pragma once
+
+#include <cmath>
 
 #include "lbm_common.cuh"
 
@@ -14,18 +17,34 @@ constexpr int OBS_BLOCK = 256;
 constexpr int OBS_MAX_BLOCKS = 608;
 constexpr int OBS_FINAL_THREADS = NOBS * 32;  // k_obs_final: one warp per slot
 
+// Pressure probe in FP32 (the kernels do no FP64 arithmetic per thread):
+// centre, squared inner and outer radii, G; probe = 0 when no cell can fall
+// inside the inner or outside the outer sphere.
 struct ObsArgs {
-    double cx, cy, cz, rin2, rout2, G;
+    float cx, cy, cz, rin2, rout2, G;
+    int probe;
 };
+inline ObsArgs obs_args(const double c[3], double r_in, double r_out, double G, long long n)
+{
+    ObsArgs O;
+    O.cx = (float)c[0];
+    O.cy = (float)c[1];
+    O.cz = (float)c[2];
+    O.rin2 = (float)(r_in * r_in);
+    O.rout2 = (float)std::fmin(r_out * r_out, 3.0e38);
+    O.G = (float)G;
+    O.probe = (r_in * r_in > 0.0 || r_out * r_out < 3.0 * (double)n * (double)n) ? 1 : 0;
+    return O;
+}
 
 // Grid-stride pass over the [6][n] fields (rhoA, rhoB, ux, uy, uz, Sw): one
-// row of NOBS partials per block in `partial`.
-__global__ void __launch_bounds__(OBS_BLOCK) k_obs_partial(DevParams P, ObsArgs O, const uint8_t *__restrict__ type,
+// row of NOBS float-float partials (hi, lo) per block in `partial`.
+__global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsArgs O, const uint8_t *__restrict__ type,
                               const float *__restrict__ phi, const float *__restrict__ macro,
-                              double *__restrict__ partial);
+                              float2 *__restrict__ partial);
 // One block of OBS_FINAL_THREADS: sums the nblocks rows of `partial` in a fixed
-// order into out[NOBS].
-__global__ void __launch_bounds__(OBS_FINAL_THREADS) k_obs_final(const double *__restrict__ partial, int nblocks,
+// order, in float-float, into out[NOBS] (FP64).
+__global__ void __launch_bounds__(OBS_FINAL_THREADS) k_obs_final(const float2 *__restrict__ partial, int nblocks,
                                                                 double *__restrict__ out);
 
 int obs_blocks(int n);
