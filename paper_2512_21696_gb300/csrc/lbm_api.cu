@@ -298,6 +298,8 @@ int lbm_create(lbm_ctx **out, const lbm_params *p)
     if (e == cudaSuccess) e = cudaMalloc(&ctx->macro, 6 * N * sizeof(float));
     ctx->red_blocks = lbm::obs_blocks(ctx->n);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->red, (size_t)(ctx->red_blocks + 1) * lbm::NOBS_HOST * sizeof(double));
+    // zero: the reduction's completion count starts there
+    if (e == cudaSuccess) e = cudaMemset(ctx->red, 0, (size_t)(ctx->red_blocks + 1) * lbm::NOBS_HOST * sizeof(double));
     if (e != cudaSuccess) {
         int code = cuda_fail(e, "lbm_create allocation");
         lbm_destroy(ctx);

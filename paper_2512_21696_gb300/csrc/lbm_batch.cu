@@ -412,6 +412,8 @@ int lbm_batch_create(lbm_batch **out, int nruns, const lbm_params *runs)
     if (e == cudaSuccess) e = cudaMalloc(&b->macro, 6 * N * sizeof(float));
     const int red_blocks = lbm::obs_blocks(max_n);
     if (e == cudaSuccess) e = cudaMalloc(&b->red, (size_t)(red_blocks + 1) * lbm::NOBS_HOST * sizeof(double));
+    // zero: the reduction's completion count starts there
+    if (e == cudaSuccess) e = cudaMemset(b->red, 0, (size_t)(red_blocks + 1) * lbm::NOBS_HOST * sizeof(double));
     if (e != cudaSuccess) {
         const int code = cuda_fail(e, "lbm_batch_create allocation");
         lbm_batch_destroy(b);

@@ -13,8 +13,10 @@
 // process exits.  Its device address is resolved once per device with
 // cudaGetSymbolAddress by the first call on that device (host code must not
 // use the symbol itself: on the host it only names a stand-in).  Each call
-// overwrites every slot it later reads, so nothing needs clearing; calls that
-// overlap on the GPU (for example on two streams) share the array and race.
+// overwrites every slot it later reads; the one slot that must start at zero,
+// the completion count in the final row, is zero at load and reset by each
+// call's last block.  Calls that overlap on the GPU (for example on two
+// streams) share the array and race.
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -70,8 +72,7 @@ extern "C" LBM_API int lbm_observables_noalloc(const float *fields, const uint8_
     float2 *partial = reinterpret_cast<float2 *>(scratch);  // a float-float pair per double slot
     double *final_row = scratch + (size_t)lbm::OBS_MAX_BLOCKS * lbm::NOBS;
     cudaStream_t s = (cudaStream_t)stream;
-    lbm::k_obs_partial<<<nb, lbm::OBS_BLOCK, 0, s>>>(P, O, type, phi, fields, partial);
-    lbm::k_obs_final<<<1, lbm::OBS_FINAL_THREADS, 0, s>>>(partial, nb, final_row);
+    lbm::k_obs_partial<<<nb, lbm::OBS_BLOCK, 0, s>>>(P, O, type, phi, fields, partial, final_row);
     if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
     double v[lbm::NOBS];
     if (cudaMemcpyAsync(v, final_row, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LBM_ERR_CUDA;

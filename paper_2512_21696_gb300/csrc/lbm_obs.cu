@@ -8,10 +8,11 @@
 //                warp-shuffle and shared-memory block reduction, one row of
 //                float-float partials per block in the reduction scratch (a
 //                pair in each double slot);
-// k_obs_final:   one block, one warp per slot: each lane sums a fixed
-//                subset of the rows, then the warp combines the lanes in a
-//                fixed order (deterministic), in float-float; each slot's
-//                result is converted to FP64 once.
+//                the last block to finish (an atomic count in the output
+//                row's spare slot) sums the rows, one warp per slot: each lane
+//                a fixed subset of the rows, then the warp in a fixed order
+//                (deterministic), in float-float; each slot's result is
+//                converted to FP64 once.
 #include <cfloat>
 
 #include "lbm_context.h"
@@ -44,7 +45,8 @@ __global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsAr
                                                            const uint8_t *__restrict__ type,
                                                            const float *__restrict__ phi,
                                                            const float *__restrict__ macro,
-                                                           float2 *__restrict__ partial)
+                                                           float2 *__restrict__ partial,
+                                                           double *__restrict__ out)
 {
     __shared__ float2 sh[NOBS * 32];
     // slots 0-7, 9, 11 summed in float-float; 10, 12, 13 are counts
@@ -143,22 +145,33 @@ __global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsAr
             if (lane == 0) partial[(size_t)blockIdx.x * NOBS + k] = make_float2(v.hi, v.lo);
         }
     }
-}
 
-__global__ void __launch_bounds__(OBS_FINAL_THREADS) k_obs_final(const float2 *__restrict__ partial, int nblocks,
-                                                                double *__restrict__ out)
-{
-    const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;  // warp k sums slot k
-    ff v = {0.f, 0.f};
-#pragma unroll 8
-    for (int b = lane; b < nblocks; b += 32) {  // unrolled: the loads go out together
-        const float2 x = partial[(size_t)b * NOBS + k];
-        if (k == SLOT_MAX) v.hi = fmaxf(v.hi, x.x);
-        else v = ff_add(v, ff{x.x, x.y});
+    // ---- the block that finishes last sums the rows into out ----
+    // Thread 0 wrote this block's row; the fence makes it visible device-wide
+    // before the count, and the last block to count reads every row from L2.
+    __shared__ unsigned int s_last;
+    unsigned int *done = reinterpret_cast<unsigned int *>(out + SLOT_COUNTER);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(done, 1u) == gridDim.x - 1 ? 1u : 0u;
     }
-    if (k == SLOT_MAX) v.hi = warp_max_f(v.hi);
-    else v = warp_sum_ff(v);
-    if (lane == 0) out[k] = (double)v.hi + (double)v.lo;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // warp w sums slots w, w + nw, ...: lanes over a fixed subset of the rows,
+    // then the warp in a fixed order (deterministic)
+    for (int k = warp; k < NOBS; k += nw) {
+        ff v = {0.f, 0.f};
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
+            const float2 x = __ldcg(&partial[(size_t)b * NOBS + k]);
+            if (k == SLOT_MAX) v.hi = fmaxf(v.hi, x.x);
+            else v = ff_add(v, ff{x.x, x.y});
+        }
+        if (k == SLOT_MAX) v.hi = warp_max_f(v.hi);
+        else v = warp_sum_ff(v);
+        // the counter's slot goes back to zero for the next reduction
+        if (lane == 0) out[k] = k == SLOT_COUNTER ? 0.0 : (double)v.hi + (double)v.lo;
+    }
 }
 
 int obs_blocks(int n)
@@ -169,7 +182,8 @@ int obs_blocks(int n)
 }
 
 // Fills host_out16 (synchronises the stream).  red must hold
-// (obs_blocks(n) + 1) * NOBS doubles.
+// (obs_blocks(n) + 1) * NOBS doubles, zero when allocated (the completion
+// counter of each reduction lives in its output row and returns to zero).
 cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16) { return launch_observables(ctx, host_out16, true); }
 
 cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16, bool sync)
@@ -181,12 +195,9 @@ cudaError_t launch_observables(lbm_ctx *ctx, double *host_out16, bool sync)
     double *out = ctx->red + (size_t)nb * NOBS;
     cudaEvent_t e0;
     prof_begin(ctx, "k_obs_partial", &e0);
-    k_obs_partial<<<nb, OBS_BLOCK, 0, ctx->stream>>>(ctx->dp, O, ctx->type, ctx->phi, ctx->macro, partial);
+    k_obs_partial<<<nb, OBS_BLOCK, 0, ctx->stream>>>(ctx->dp, O, ctx->type, ctx->phi, ctx->macro, partial, out);
     prof_end(ctx, "k_obs_partial", e0);
-    prof_begin(ctx, "k_obs_final", &e0);
-    k_obs_final<<<1, OBS_FINAL_THREADS, 0, ctx->stream>>>(partial, nb, out);
-    prof_end(ctx, "k_obs_final", e0);
-    ctx->launches += 2;
+    ctx->launches += 1;
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     err = cudaMemcpyAsync(host_out16, out, NOBS * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);

@@ -13,9 +13,9 @@ constexpr int NOBS = 16;
 //        8 max |u|; 9 sum p inside; 10 count inside; 11 sum p outside;
 //        12 count outside; 13 non-finite count
 constexpr int SLOT_MAX = 8;
+constexpr int SLOT_COUNTER = 15;  // of the output row: blocks done (zero between reductions)
 constexpr int OBS_BLOCK = 256;
 constexpr int OBS_MAX_BLOCKS = 608;
-constexpr int OBS_FINAL_THREADS = NOBS * 32;  // k_obs_final: one warp per slot
 
 // Pressure probe in FP32 (the kernels do no FP64 arithmetic per thread):
 // centre, squared inner and outer radii, G; probe = 0 when no cell can fall
@@ -38,14 +38,12 @@ inline ObsArgs obs_args(const double c[3], double r_in, double r_out, double G, 
 }
 
 // Grid-stride pass over the [6][n] fields (rhoA, rhoB, ux, uy, uz, Sw): one
-// row of NOBS float-float partials (hi, lo) per block in `partial`.
+// row of NOBS float-float partials (hi, lo) per block in `partial`; the last
+// block to finish sums the rows in a fixed order into out[NOBS] (FP64).
+// out[SLOT_COUNTER] must be zero at launch and is zero again at exit.
 __global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsArgs O, const uint8_t *__restrict__ type,
                               const float *__restrict__ phi, const float *__restrict__ macro,
-                              float2 *__restrict__ partial);
-// One block of OBS_FINAL_THREADS: sums the nblocks rows of `partial` in a fixed
-// order, in float-float, into out[NOBS] (FP64).
-__global__ void __launch_bounds__(OBS_FINAL_THREADS) k_obs_final(const float2 *__restrict__ partial, int nblocks,
-                                                                double *__restrict__ out);
+                              float2 *__restrict__ partial, double *__restrict__ out);
 
 int obs_blocks(int n);
 
