@@ -813,16 +813,6 @@ def run_imbibition2d(args):
 
 
 # ------------------------------------------------- 2-D fibre zigzag (D2Q9)
-def zigzag_pathway(nx=120, ny=180, half_width=10.0, amp=20.0, period=90.0):
-    """The open pathway of the Sec. I.B set-up on one plane: pore cells within
-    half_width (in x) of the sinusoidal centre line x_c(y) = nx/2 + amp
-    sin(2 pi y / period); the two fibre bundles on either side, out to the
-    walls, are gray."""
-    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
-    xc = nx / 2.0 - 0.5 + amp * np.sin(2.0 * np.pi * y / period)
-    return (np.abs(x - xc) <= half_width)[None]
-
-
 def run_zigzag2d(args):
     """Single-phase flow through the zigzag pathway between two wavy-fibre
     bundles (Sec. I.B, Sec. III.E) on D2Q9: the pathway is open pore
@@ -838,11 +828,8 @@ def run_zigzag2d(args):
     from paper_2512_21696_gb300 import lbm, synth
     torch.cuda.set_device(0)
     nx, ny, lo, hi = 120, 180, 0.03, 1.0
-    path = zigzag_pathway(nx, ny)
-    cell = np.full((1, ny + 2, nx), synth.GRAY, np.uint8)
-    cell[0, 1:-1, :][path[0]] = synth.PORE
-    cell[0, -1, :], cell[0, 0, :] = synth.INLET, synth.OUTLET
-    phi_all = np.where(cell == synth.GRAY, 0.95, 1.0).astype(np.float32)
+    cell, phi_all, path_all = synth.zigzag_pathway_geometry(nx, ny)
+    path = path_all[:, 1:-1, :]
     rho_in = hi * 0.740 / 0.733
     stream = torch.cuda.current_stream()
     res, total_ms = {}, 0.0

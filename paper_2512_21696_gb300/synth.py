@@ -261,3 +261,23 @@ def cosine_porosity(shape, phi0: float, amp: float, k) -> np.ndarray:
     nz, ny, nx = shape
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     return phi0 + amp * np.cos(k[0] * x + k[1] * y + k[2] * z)
+
+
+def zigzag_pathway_geometry(nx=120, ny=180, half_width=10.0, amp=20.0, period=90.0, phi_bundle=0.95):
+    """The two-dimensional fibre-bundle case of Sec. I.B / Sec. III.E on one
+    plane: an open pathway (pore cells within half_width in x of the
+    sinusoidal centre line x_c(y) = nx/2 + amp sin(2 pi y / period)) between
+    two gray bundles of porosity phi_bundle that reach the walls, with a row
+    of inlet cells above (y = ny + 1) and of outlet cells below (y = 0).
+    Returns (cell, phi, path): shape (1, ny + 2, nx) each, path marking the
+    pathway's pore cells."""
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    xc = nx / 2.0 - 0.5 + amp * np.sin(2.0 * np.pi * y / period)
+    inner = np.abs(x - xc) <= half_width
+    cell = np.full((1, ny + 2, nx), GRAY, np.uint8)
+    cell[0, 1:-1, :][inner] = PORE
+    cell[0, -1, :], cell[0, 0, :] = INLET, OUTLET
+    phi = np.where(cell == GRAY, phi_bundle, 1.0).astype(np.float32)
+    path = np.zeros(cell.shape, bool)
+    path[0, 1:-1, :] = inner
+    return cell, phi, path
