@@ -149,11 +149,14 @@ __global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsAr
     // ---- the block that finishes last sums the rows into out ----
     // Thread 0 wrote this block's row; the fence makes it visible device-wide
     // before the count, and the last block to count reads every row from L2.
+    // The count wraps to zero at the last block (atomicInc), so even a count
+    // left over by a reduction that raced with another on the same scratch
+    // cannot outlive one call.
     __shared__ unsigned int s_last;
     unsigned int *done = reinterpret_cast<unsigned int *>(out + SLOT_COUNTER);
     if (threadIdx.x == 0) {
         __threadfence();
-        s_last = atomicAdd(done, 1u) == gridDim.x - 1 ? 1u : 0u;
+        s_last = atomicInc(done, gridDim.x - 1) == gridDim.x - 1 ? 1u : 0u;
     }
     __syncthreads();
     if (!s_last) return;
