@@ -80,3 +80,38 @@ def test_eigenvector_derivative_formula():
 
     fd = (top(B @ B.T + h * D) - top(B @ B.T - h * D)) / (2 * h) @ wvec.numpy()
     assert abs((M.grad.numpy() * D).sum() - fd) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_torch_geometry_matches_c_oracle_on_flat_blocks():
+    """The geometry of the PyTorch statement (Eqs. 5-7) against the C oracle
+    on uniform-porosity blocks: no axis in the flat interiors, the same
+    tensor everywhere (the two sum the gradient stencil independently)."""
+    case = LC.flat_blocks("d3q19", shape=(6, 10, 30))
+    _, _, ost = LC.run_oracle(case, 0)
+    cv = case.curves[0]
+    geo = A.geometry(case.cell, torch.tensor(case.phi32.astype(np.float64)), cv, case.s["c_g"])
+    kinv = geo["kinv"].detach().numpy()  # [z, y, x, 3, 3]
+    gray = case.cell == 2
+    ok = np.moveaxis(ost["kinv"], (0, 1), (-2, -1))
+    assert np.abs(kinv - ok)[gray].max() <= 1e-12 * np.abs(ok[gray]).max()
+    flat = gray & (ost["iso"] == 1)
+    assert flat.sum() > 0.3 * gray.sum()
+    off = ~np.eye(3, dtype=bool)
+    assert np.all(kinv[flat][:, off] == 0.0)
+
+
+def test_zigzag_pathway_geometry():
+    """The Sec. I.B / III.E input: a connected open pathway a sixth of the
+    width, gray bundles of phi = 0.95 out to the walls, reservoir rows."""
+    from paper_2512_21696_gb300 import synth
+    cell, phi, path = synth.zigzag_pathway_geometry()
+    assert cell.shape == phi.shape == path.shape == (1, 182, 120)
+    assert np.all(cell[0, 0] == synth.OUTLET) and np.all(cell[0, -1] == synth.INLET)
+    inner = cell[0, 1:-1]
+    assert set(np.unique(inner)) == {synth.PORE, synth.GRAY}
+    assert np.all(path[0, 1:-1] == (inner == synth.PORE)) and not path[0, [0, -1]].any()
+    assert np.all(phi[cell == synth.GRAY] == np.float32(0.95)) and np.all(phi[cell != synth.GRAY] == 1.0)
+    rows = path[0, 1:-1]
+    assert np.all(rows.sum(axis=1) == 20)  # every row: the same width
+    assert all((rows[k] & rows[k + 1]).any() for k in range(rows.shape[0] - 1))  # connected top to bottom
+    assert not rows[:, 0].any() and not rows[:, -1].any()  # the bundles reach both walls
