@@ -9,7 +9,7 @@
 //   M = H H + c_g grad(phi) grad(phi)^T; its top eigenvector e1 is the axis
 //   of lowest permeability, K = B diag(K0/a, K0, K0) B^T, so
 //   K^-1 = (1/K0)(I + (a-1) e1 e1^T); ties (mu1 - mu2 <= 1e-12 mu1) fall back
-//   to isotropic;
+//   to isotropic; pore types with a = 1 skip the axis (K^-1 = I / K0);
 //   K0 (Kozeny-Carman), Leverett factor lamL (Eq. 5), and the residual
 //   amounts from the crossings of Pc(Sw; phi) with pc_ref_max_f*pd and
 //   pc_ref_min_f*pd (Fig. 6).
@@ -103,40 +103,45 @@ __global__ void k_geometry(DevParams P, CurveTable T, double c_g, const uint8_t 
     if (type[c] != CELL_GRAY) return;
     const int x = c % P.nx, y = (c / P.nx) % P.ny, z = c / (P.nx * P.ny);
     const double ph = (double)phi[c];
-    // central differences over the opposite pairs (i odd, opp(i) = i + 1): a
-    // flat neighbourhood gives exactly zero, never round-off with an axis
-    double g[3] = {0.0, 0.0, 0.0};
-    for (int i = 1; i < Q; i += 2) {
-        const double v = phi_of(type, phi, nbr(P, x, y, z, cx(i), cy(i), cz(i))) -
-                         phi_of(type, phi, nbr(P, x, y, z, -cx(i), -cy(i), -cz(i)));
-        g[0] += 3.0 * wgt_d(i) * cx(i) * v;
-        g[1] += 3.0 * wgt_d(i) * cy(i) * v;
-        g[2] += 3.0 * wgt_d(i) * cz(i) * v;
-    }
-    double H[3][3];
-    for (int a = 0; a < 3; ++a) {
-        int ea[3] = {0, 0, 0};
-        ea[a] = 1;
-        H[a][a] = phi_of(type, phi, nbr(P, x, y, z, ea[0], ea[1], ea[2])) - 2.0 * ph +
-                  phi_of(type, phi, nbr(P, x, y, z, -ea[0], -ea[1], -ea[2]));
-        for (int b = a + 1; b < 3; ++b) {
-            int eb[3] = {0, 0, 0};
-            eb[b] = 1;
-            const double pp = phi_of(type, phi, nbr(P, x, y, z, ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2]));
-            const double pm = phi_of(type, phi, nbr(P, x, y, z, ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2]));
-            const double mp = phi_of(type, phi, nbr(P, x, y, z, eb[0] - ea[0], eb[1] - ea[1], eb[2] - ea[2]));
-            const double mm = phi_of(type, phi, nbr(P, x, y, z, -ea[0] - eb[0], -ea[1] - eb[1], -ea[2] - eb[2]));
-            H[a][b] = H[b][a] = 0.25 * (pp - pm - mp + mm);
-        }
-    }
-    double M[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-            M[a][b] = H[a][0] * H[0][b] + H[a][1] * H[1][b] + H[a][2] * H[2][b] + c_g * g[a] * g[b];
     const int pt = ptype ? (int)ptype[c] : 0;
     const lbm_constitutive cv = T.c[pt];
     double e[3] = {0.0, 0.0, 0.0};
-    const bool axis = top_eigvec(M, e);
+    bool axis = false;
+    // the axis matters only where the pore type is anisotropic: with a = 1,
+    // K^-1 = I / K0 whatever e1 is, so the stencils and the eigenvector are skipped
+    if (cv.aniso != 1.0) {
+        // central differences over the opposite pairs (i odd, opp(i) = i + 1): a
+        // flat neighbourhood gives exactly zero, never round-off with an axis
+        double g[3] = {0.0, 0.0, 0.0};
+        for (int i = 1; i < Q; i += 2) {
+            const double v = phi_of(type, phi, nbr(P, x, y, z, cx(i), cy(i), cz(i))) -
+                             phi_of(type, phi, nbr(P, x, y, z, -cx(i), -cy(i), -cz(i)));
+            g[0] += 3.0 * wgt_d(i) * cx(i) * v;
+            g[1] += 3.0 * wgt_d(i) * cy(i) * v;
+            g[2] += 3.0 * wgt_d(i) * cz(i) * v;
+        }
+        double H[3][3];
+        for (int a = 0; a < 3; ++a) {
+            int ea[3] = {0, 0, 0};
+            ea[a] = 1;
+            H[a][a] = phi_of(type, phi, nbr(P, x, y, z, ea[0], ea[1], ea[2])) - 2.0 * ph +
+                      phi_of(type, phi, nbr(P, x, y, z, -ea[0], -ea[1], -ea[2]));
+            for (int b = a + 1; b < 3; ++b) {
+                int eb[3] = {0, 0, 0};
+                eb[b] = 1;
+                const double pp = phi_of(type, phi, nbr(P, x, y, z, ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2]));
+                const double pm = phi_of(type, phi, nbr(P, x, y, z, ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2]));
+                const double mp = phi_of(type, phi, nbr(P, x, y, z, eb[0] - ea[0], eb[1] - ea[1], eb[2] - ea[2]));
+                const double mm = phi_of(type, phi, nbr(P, x, y, z, -ea[0] - eb[0], -ea[1] - eb[1], -ea[2] - eb[2]));
+                H[a][b] = H[b][a] = 0.25 * (pp - pm - mp + mm);
+            }
+        }
+        double M[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                M[a][b] = H[a][0] * H[0][b] + H[a][1] * H[1][b] + H[a][2] * H[2][b] + c_g * g[a] * g[b];
+        axis = top_eigvec(M, e);
+    }
     const double sa = axis ? sqrt(cv.aniso - 1.0) : 0.0;
     const double K0 = kozeny(cv, ph);
     const double kref = kozeny(cv, cv.phi_ref);
