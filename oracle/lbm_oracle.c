@@ -31,6 +31,11 @@
  *     -Pc(Sw) rho_r n H and the viscous resistance, the latter made tensorial
  *     by Eqs. 6-7 (principal axis from the Hessian and gradient of porosity,
  *     abstract and Sec. II) and solved semi-implicitly for the velocity.
+ *     Reading: the top eigenvector of M = H H + c_g grad phi grad phi^T is
+ *     the low-permeability axis, a tie of the two largest eigenvalues
+ *     (within 1e-12 of the largest, floor 1e-30) means no axis, and the
+ *     gradient is summed over opposite velocity pairs so that a flat
+ *     neighbourhood gives M = 0 exactly.
  *   - Residual components (Sec. II, Eq. 5 and Fig. 6): crossings of the
  *     Leverett-scaled Pc(Sw; phi) with Pc_ref,max / Pc_ref,min give the
  *     residual water / oil amounts, switched on by a hysteresis on the local
