@@ -241,7 +241,8 @@ LBM_API int lbm_init_fields(lbm_ctx *ctx, const float *rhoA, const float *rhoB, 
  * lbm_init_fields, lbm_load_state, lbm_set_kernel, lbm_profile); the
  * replayed kernels are the same launches, so the result is bit-identical and
  * lbm_launch_count counts them.  A failed capture falls back to direct
- * launches for the rest of the context's life. */
+ * launches for the rest of the context's life; while the caller's stream is
+ * being captured (the caller's own graph) the steps are launched directly. */
 LBM_API int lbm_step(lbm_ctx *ctx, int nsteps);
 
 /* Pressure boundaries: the densities held in the LBM_CELL_INLET and

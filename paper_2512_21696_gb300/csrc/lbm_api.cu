@@ -571,9 +571,19 @@ int lbm_step(lbm_ctx *ctx, int nsteps)
     // small lattices: after one direct step (which also resolves each
     // kernel's launch configuration), replay GRAPH_STEPS-step graphs while
     // more than GRAPH_STEPS steps remain; the last steps, which write the
-    // fields, run directly
-    if (!ctx->view && !ctx->profiling && !ctx->graph_off && ctx->n <= lbm::GRAPH_MAX_CELLS &&
-        nsteps > lbm::GRAPH_STEPS + 1) {
+    // fields, run directly.  A caller capturing its own stream gets direct
+    // launches (a capture of ours inside theirs could invalidate it).
+    bool replay = !ctx->view && !ctx->profiling && !ctx->graph_off && ctx->n <= lbm::GRAPH_MAX_CELLS &&
+                  nsteps > lbm::GRAPH_STEPS + 1;
+    if (replay) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            cs = cudaStreamCaptureStatusActive;
+        }
+        replay = cs == cudaStreamCaptureStatusNone;
+    }
+    if (replay) {
         LBM_CUDA(step_once(ctx, false));
         k = 1;
         while (nsteps - k > lbm::GRAPH_STEPS) {

@@ -120,3 +120,44 @@ def test_graph_replay_matches_the_oracle():
     fl = case.cell != synth.SOLID
     for g, o in ((ga, oa), (gb, ob), (gu, ou), (gs, osw)):
         assert rel_l2(g, o, fl) <= 1e-5
+
+
+def test_lbm_step_inside_a_callers_graph_capture():
+    """A caller capturing its own stream gets plain launches inside its graph
+    (no nested capture of ours): two direct steps, 40 steps captured by the
+    caller and replayed twice equal 82 steps stepped directly."""
+    import torch
+    from paper_2512_21696_gb300 import lbm
+    case = LC.mixed2d(shape=(1, 24, 30), seed=7)
+    s = torch.cuda.Stream()
+    ref = _open(case)
+    try:
+        lbm.lbm_step(ref, 82)
+        want = [np.array(x, copy=True) for x in lbm.lbm_get_fields(ref)]
+    finally:
+        ref.close()
+    p = LC.gpu_params(case)
+    p.stream = s.cuda_stream
+    from paper_2512_21696_gb300 import lbm as L
+    ctx = L.lbm_create(p)
+    try:
+        for k, cv in enumerate(case.curves):
+            L.lbm_set_constitutive(ctx, k, L.lbm_default_constitutive(
+                kc_d=cv["kc_d"], pd=cv["pd"], lam=cv["lam"], swr=cv["swr"], nw=cv["nw"], nn=cv["nn"],
+                phi_ref=cv["phi_ref"], pc_ref_max_f=cv["f_max"], pc_ref_min_f=cv["f_min"], aniso=cv["aniso"],
+                thomeer_g=cv["thomeer_g"]))
+        L.lbm_set_geometry(ctx, case.cell, case.phi32, case.ptype)
+        L.lbm_init_fields(ctx, case.rhoA32, case.rhoB32, case.u32)
+        L.lbm_step(ctx, 2)  # both kernel variants resolve their launch configuration outside the capture
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            L.lbm_step(ctx, 40)
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        got = L.lbm_get_fields(ctx)
+        for x, y in zip(want, got):
+            np.testing.assert_array_equal(x, y)
+    finally:
+        ctx.close()
