@@ -1,0 +1,83 @@
+"""The oracle's pins have teeth: planted mistakes are caught (no GPU).
+
+Each case copies the C oracle, plants one plausible mistake in it (a sign,
+a factor, a dropped term, a wrong index, a swapped argument), builds the
+mutant with gcc, and runs in a fresh process the pins of
+``test_oracle_pins.py`` that should catch it, with the oracle wrapper
+pointed at the mutant.  The pins must fail (pytest exit status 1: failures,
+not errors).  A control run of the same pins against the unchanged source
+must pass, so that the failures come from the mistakes and not from the
+harness.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+REPO = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TESTS = os.path.join(REPO, "tests")
+SRC = os.path.join(REPO, "oracle", "lbm_oracle.c")
+PINS = os.path.join(TESTS, "test_oracle_pins.py")
+
+# (name, text in the oracle, planted replacement, pins expected to catch it)
+MUTANTS = [
+    ("relaxation_rate", "(1.0 - 1.0 / tau) * L->w[i] * QP", "(1.0 - 0.5 / tau) * L->w[i] * QP",
+     "test_shear_wave_decay_gives_lattice_viscosity"),
+    ("force_term_half", "+ 0.5 * force_term(L, i, u, F);", "+ 1.0 * force_term(L, i, u, F);",
+     "test_collision_moments_match_bgk_with_force"),
+    ("shan_chen_sign", "T[T_SC][a][d] = -p->G * r[a] * ga;", "T[T_SC][a][d] = p->G * r[a] * ga;",
+     "test_shan_chen_force_on_cosine_field"),
+    ("csf_curvature_sign", "p->kappa * (-div)", "p->kappa * (div)",
+     "test_csf_force_on_cylinder_matches_continuum"),
+    ("anisotropy_minus_one", "double am1 = cv->aniso - 1.0;", "double am1 = cv->aniso;",
+     "test_tensorial_resistivity_direction"),
+    ("kozeny_carman_power", "(180.0 * (1.0 - phi) * (1.0 - phi))", "(180.0 * (1.0 - phi))",
+     "test_darcy_uniform_gray"),
+    ("hysteresis_threshold", "if (st->wetflag[c] && s < p->s_lo) {", "if (st->wetflag[c] && s < p->s_hi) {",
+     "test_residual_hysteresis_switches"),
+    ("bounce_back_slot", "st->f[((long)a * Q + opp[i]) * n + c]", "st->f[((long)a * Q + i) * n + c]",
+     "test_poiseuille_profile"),
+    ("porosity_gradient_scale", "L->w[i] * (vp - vm) * L->cv[i][d] / CS2;", "L->w[i] * (vp - vm) * L->cv[i][d];",
+     "test_principal_axis_on_cosine_porosity"),
+    ("d2q9_diagonal_weight", "(len2 == 1 ? 1.0 / 9.0 : 1.0 / 36.0)", "(len2 == 1 ? 1.0 / 9.0 : 1.0 / 18.0)",
+     "test_d2q9_is_the_plane_projection_of_d3q19_at_unit_tau"),
+    ("reservoirs_swapped", "return st->type[c] == INLET ? st->p.rho_in[a] : st->p.rho_out[a];",
+     "return st->type[c] == INLET ? st->p.rho_out[a] : st->p.rho_in[a];",
+     "test_darcy_between_pressure_reservoirs"),
+]
+
+
+def _build(tmp_path, text):
+    c = tmp_path / "oracle_variant.c"
+    c.write_text(text)
+    so = tmp_path / "liborc_variant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", str(c), "-o", str(so), "-lm"],
+                   check=True, capture_output=True)
+    return str(so)
+
+
+def _run_pins(so, pins):
+    code = (f"import sys; sys.path[:0] = [{REPO!r}, {TESTS!r}]\n"
+            f"import oracle\n"
+            f"oracle.build = lambda force=False: {so!r}\n"
+            f"import pytest\n"
+            f"sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', {PINS!r}, '-k', {pins!r}]))\n")
+    return subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=REPO)
+
+
+def test_control_unchanged_oracle_passes_the_pins(tmp_path):
+    with open(SRC) as f:
+        so = _build(tmp_path, f.read())
+    r = _run_pins(so, " or ".join(m[3] for m in MUTANTS))
+    assert r.returncode == 0, r.stdout[-3000:]
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_a_planted_mistake(tmp_path, name, old, new, pins):
+    with open(SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"{name}: the mutated text must occur exactly once"
+    so = _build(tmp_path, text.replace(old, new))
+    r = _run_pins(so, pins)
+    assert r.returncode == 1, f"{name}: pins {pins} did not fail (exit {r.returncode})\n{r.stdout[-3000:]}"
