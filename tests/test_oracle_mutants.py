@@ -45,6 +45,22 @@ MUTANTS = [
     ("reservoirs_swapped", "return st->type[c] == INLET ? st->p.rho_in[a] : st->p.rho_out[a];",
      "return st->type[c] == INLET ? st->p.rho_out[a] : st->p.rho_in[a];",
      "test_darcy_between_pressure_reservoirs"),
+    ("leverett_square_root", "return sqrt((kref / cv->phi_ref) / (k / phi));",
+     "return (kref / cv->phi_ref) / (k / phi);", "test_leverett_invariance_and_residual_crossings"),
+    ("thomeer_log_base", "double e = -cv->thomeer_g / log(1.0 - se);",
+     "double e = -cv->thomeer_g / log10(1.0 - se);", "test_thomeer_capillary_pressure_inside_the_curve"),
+    ("thomeer_crossing_sign", "1.0 - exp(-cv->thomeer_g / log10(ratio))", "1.0 - exp(cv->thomeer_g / log10(ratio))",
+     "test_thomeer_residual_crossings"),
+    ("mss_direction", "double sgn = a == w ? 1.0 : -1.0;", "double sgn = a == w ? -1.0 : 1.0;",
+     "test_mass_sink_source_special_cases"),
+    ("mss_background", "double I = (4.0 * rw * rn - Ib) / (1.0 - Ib);", "double I = (4.0 * rw * rn) / (1.0 - Ib);",
+     "test_mass_sink_source_special_cases"),
+    ("saturation_weight", "double phc = st->type[c] == GRAY ? st->phi[c] : 1.0;", "double phc = 1.0;",
+     "test_observables_are_plain_sums"),
+    ("capillary_sign", "T[T_CAP][a][d] = -Pc * (r[a] / rt)", "T[T_CAP][a][d] = Pc * (r[a] / rt)",
+     "test_capillary_force_flat_interface_telescopes"),
+    ("drag_implicit_half", "A[a][b] = (a == b ? rt : 0.0) + 0.5 * R[a][b];",
+     "A[a][b] = (a == b ? rt : 0.0) + 1.0 * R[a][b];", "test_darcy_uniform_gray"),
 ]
 
 

@@ -356,6 +356,35 @@ def test_capillary_force_flat_interface_telescopes():
         assert abs(total - (-0.02 * scale * jump)) < tol * 0.02 * scale
 
 
+def test_thomeer_capillary_pressure_inside_the_curve():
+    """Cell by cell, the capillary force of Eq. 1 summed over the components is
+    -Pc(Sw) grad(At) / 2 (H = |grad At| / 2, the rho_r / rho_t weights sum to
+    one), so Pc can be read off and set against Thomeer's hyperbola
+    Pc = Pe 10^min(-G / ln(1 - Se), 1) at interior saturations, on both sides
+    of the cap (phi = phi_ref: Pe = Pd)."""
+    nz = 32
+    shape = (nz, 2, 2)
+    z = np.arange(nz)
+    A = (-0.9 * np.cos(2 * np.pi * z / nz))[:, None, None] * np.ones(shape)
+    p = O.make_params(shape, at_cut=1.0, wet=1)
+    cell = np.full(shape, synth.GRAY, np.uint8)
+    g, pd, swr = 0.5, 0.02, 0.15
+    o = _rest_state(p, cell, 0.5 * (1 - A), 0.5 * (1 + A), phi=np.full(shape, 0.35),
+                    curves=[O.make_curve(thomeer_g=g, phi_ref=0.35, pd=pd, swr=swr)])
+    Fz = (o.force_term(O.TERM_CAP, 0)[2] + o.force_term(O.TERM_CAP, 1)[2])[:, 0, 0]
+    Az = A[:, 0, 0]
+    dAt = 0.5 * (np.roll(Az, -1) - np.roll(Az, 1))  # the isotropic stencil on a z-only field
+    r_lo, r_hi = 0.03 / 1.03, 1.0 / 1.03
+    s = np.clip(((1 + Az) / 2 - r_lo) / (r_hi - r_lo), 0.0, 1.0)  # wetting B at rho_B / rho_t
+    se = np.clip((s - swr) / (1 - swr), 1e-2, 1.0)
+    expect = pd * 10.0 ** np.minimum(-g / np.log(1.0 - se), 1.0)
+    use = np.abs(dAt) > 1e-3
+    got = -2.0 * Fz[use] / dAt[use]
+    np.testing.assert_allclose(got, expect[use], rtol=1e-10)
+    e = -g / np.log(1.0 - se[use])
+    assert (e < 1.0).sum() >= 4 and (e > 1.0).sum() >= 4  # both branches are exercised
+
+
 @pytest.mark.parametrize("lattice", ["d3q19", "d2q9"])
 def test_csf_force_on_cylinder_matches_continuum(lattice):
     """Eq. 4 on a smooth cylindrical interface: div n = 1/r in two dimensions.
