@@ -61,6 +61,18 @@ MUTANTS = [
      "test_capillary_force_flat_interface_telescopes"),
     ("drag_implicit_half", "A[a][b] = (a == b ? rt : 0.0) + 0.5 * R[a][b];",
      "A[a][b] = (a == b ? rt : 0.0) + 1.0 * R[a][b];", "test_darcy_uniform_gray"),
+    ("corey_exponents_swapped", "kr[w] = pow(se, cv->nw);", "kr[w] = pow(se, cv->nn);",
+     "test_two_component_darcy_with_corey_permeabilities"),
+    ("wall_density_of_other_component", "return is_wall(st, m) ? st->p.rho_wall[a] : st->rho[a][m];",
+     "return is_wall(st, m) ? st->p.rho_wall[1 - a] : st->rho[a][m];", "test_shan_chen_force_next_to_a_wall"),
+    ("velocity_half_force", "uc[d] = (jc[d] + 0.5 * Ft) / rt;", "uc[d] = (jc[d] + 1.0 * Ft) / rt;",
+     "test_poiseuille_profile"),
+    ("csf_phi_avg", "(st->grad[a][d * n + c] / p->phi_avg[a])", "(st->grad[a][d * n + c] * p->phi_avg[a])",
+     "test_csf_force_on_cylinder_matches_continuum"),
+    ("atwood_cut_inverted", "(fabs(At_c) <= p->at_cut)", "(fabs(At_c) >= p->at_cut)",
+     "test_capillary_force_flat_interface_telescopes"),
+    ("hermite_trace_dropped", "(L->cv[i][a] * L->cv[i][b] - (a == b ? CS2 : 0.0)) * P[a][b]",
+     "(L->cv[i][a] * L->cv[i][b]) * P[a][b]", "test_collision_moments_match_bgk_with_force"),
 ]
 
 

@@ -195,6 +195,56 @@ def test_darcy_uniform_gray(phi):
     np.testing.assert_allclose(ux, expected, rtol=1e-7)
 
 
+def test_two_component_darcy_with_corey_permeabilities():
+    """A uniform mixture in a uniform gray domain under one body acceleration:
+    steady u = K0 (rho_A + rho_B) g / coef with the Eq. 1 drag coefficient
+    coef = rho_n nu_n / kr_n + rho_w nu_w / kr_w, Corey kr_w = Se^nw,
+    kr_n = (1 - Se)^nn at the local saturation (no interface, so no capillary,
+    Shan-Chen or Eq. 4 force)."""
+    g, phi, kd = 1e-6, 0.5, 10.0
+    shape = (4, 4, 4)
+    cell = np.full(shape, synth.GRAY, np.uint8)
+    p = O.make_params(shape, accel=((g, 0, 0), (g, 0, 0)), wet=1, tau=(1.0, 0.8))
+    curve = O.make_curve(kc_d=kd, swr=0.15, nw=3.0, nn=2.0)
+    o = O.Oracle(p, cell, np.full(shape, phi), curves=[curve])
+    ra, rb = 0.4, 0.6  # B wets
+    o.init_fields(np.full(shape, ra), np.full(shape, rb))
+    o.step(200)
+    r_lo, r_hi = 0.03 / 1.03, 1.0 / 1.03
+    s_w = (rb / (ra + rb) - r_lo) / (r_hi - r_lo)
+    se = (s_w - 0.15) / 0.85
+    kr_w, kr_n = se ** 3.0, (1.0 - se) ** 2.0
+    nu_a, nu_b = (1.0 - 0.5) / 3.0, (0.8 - 0.5) / 3.0
+    coef = ra * nu_a / kr_n + rb * nu_b / kr_w
+    expected = kc(phi, kd) * (ra + rb) * g / coef
+    u = o.fields()[2]
+    np.testing.assert_allclose(u[0], expected, rtol=1e-10)
+    assert np.abs(u[1:]).max() < 1e-20
+    assert abs(kr_w - kr_n) > 0.05 and abs(se ** 2 - (1 - se) ** 3) > 0.1  # the exponents matter here
+
+
+def test_shan_chen_force_next_to_a_wall():
+    """Beside a solid plane the other component's density stencil sees the
+    virtual wall density (the wetting control): for uniform fluid densities,
+    F_SC^A = -G rho^A (rho^B - rho_wall^B) / 2 towards the wall's normal, and
+    symmetrically for B; no force one cell further in."""
+    shape = (6, 4, 4)
+    cell = np.zeros(shape, np.uint8)
+    cell[0] = synth.SOLID
+    G, rw = 1.1, (0.2, 0.7)
+    p = O.make_params(shape, G=G, rho_wall=rw)
+    ra, rb = 0.3, 0.6
+    fl = cell != synth.SOLID
+    o = _rest_state(p, cell, np.where(fl, ra, 0.0), np.where(fl, rb, 0.0))
+    FA, FB = o.force_term(O.TERM_SC, 0), o.force_term(O.TERM_SC, 1)
+    # z = 1 has the wall below (-z), z = 5 above (+z, periodic): the stencil's
+    # z component is (rho(+z side) - rho(-z side)) / 2
+    np.testing.assert_allclose(FA[2, 1], -G * ra * (rb - rw[1]) / 2, rtol=1e-13)
+    np.testing.assert_allclose(FB[2, 1], -G * rb * (ra - rw[0]) / 2, rtol=1e-13)
+    np.testing.assert_allclose(FA[2, 5], -G * ra * (rw[1] - rb) / 2, rtol=1e-13)
+    assert np.abs(FA[:2]).max() < 1e-15 and np.abs(FA[2, 2:5]).max() < 1e-15
+
+
 @pytest.mark.parametrize("phi", [0.6, 0.4])
 def test_darcy_between_pressure_reservoirs(phi):
     """One component through a uniform gray column between an inlet and an
