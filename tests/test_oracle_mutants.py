@@ -4,7 +4,7 @@ Each case copies the C oracle, plants one plausible mistake in it (a sign,
 a factor, a dropped term, a wrong index, a swapped argument), builds the
 mutant with gcc, and runs in a fresh process the pins of
 ``test_oracle_pins.py`` that should catch it, with the oracle wrapper
-pointed at the mutant.  The pins must fail (pytest exit status 1: failures,
+pointed at the mutant (several mutants at a time).  The pins must fail (pytest exit status 1: failures,
 not errors).  A control run of the same pins against the unchanged source
 must pass, so that the failures come from the mistakes and not from the
 harness.
@@ -12,6 +12,7 @@ harness.
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -73,6 +74,14 @@ MUTANTS = [
      "test_capillary_force_flat_interface_telescopes"),
     ("hermite_trace_dropped", "(L->cv[i][a] * L->cv[i][b] - (a == b ? CS2 : 0.0)) * P[a][b]",
      "(L->cv[i][a] * L->cv[i][b]) * P[a][b]", "test_collision_moments_match_bgk_with_force"),
+    ("csf_region_inverted", "(p->csf_everywhere || gray)", "(p->csf_everywhere || !gray)",
+     "test_csf_acts_in_gray_cells_only_unless_everywhere"),
+    ("residual_crossings_swapped", "sw_at_pressure(cv, lamL, cv->f_max * pc_pm);",
+     "sw_at_pressure(cv, lamL, cv->f_min * pc_pm);", "test_leverett_invariance_and_residual_crossings"),
+    ("leverett_reference_porosity", "double kref = kozeny_carman(cv, cv->phi_ref);",
+     "double kref = kozeny_carman(cv, phi);", "test_leverett_invariance_and_residual_crossings"),
+    ("outlet_plane", "if (x == p->nx - 1) fout += u0;", "if (x == 0) fout += u0;",
+     "test_observables_are_plain_sums"),
 ]
 
 
@@ -91,21 +100,37 @@ def _run_pins(so, pins):
             f"oracle.build = lambda force=False: {so!r}\n"
             f"import pytest\n"
             f"sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', {PINS!r}, '-k', {pins!r}]))\n")
-    return subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=REPO)
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    return subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=900, cwd=REPO,
+                          env=env)
 
 
-def test_control_unchanged_oracle_passes_the_pins(tmp_path):
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """Builds and runs the control and every mutant, several at a time (each
+    is a separate gcc and Python process); returns name -> completed process."""
     with open(SRC) as f:
-        so = _build(tmp_path, f.read())
-    r = _run_pins(so, " or ".join(m[3] for m in MUTANTS))
+        text = f.read()
+    jobs = [("control", text, " or ".join(m[3] for m in MUTANTS))]
+    for name, old, new, pins in MUTANTS:
+        assert text.count(old) == 1, f"{name}: the mutated text must occur exactly once"
+        jobs.append((name, text.replace(old, new), pins))
+
+    def run(job):
+        name, variant, pins = job
+        return name, _run_pins(_build(tmp_path_factory.mktemp(name), variant), pins)
+
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        return dict(ex.map(run, jobs))
+
+
+def test_control_unchanged_oracle_passes_the_pins(outcomes):
+    r = outcomes["control"]
     assert r.returncode == 0, r.stdout[-3000:]
 
 
-@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_catch_a_planted_mistake(tmp_path, name, old, new, pins):
-    with open(SRC) as f:
-        text = f.read()
-    assert text.count(old) == 1, f"{name}: the mutated text must occur exactly once"
-    so = _build(tmp_path, text.replace(old, new))
-    r = _run_pins(so, pins)
+@pytest.mark.parametrize("name,pins", [(m[0], m[3]) for m in MUTANTS], ids=[m[0] for m in MUTANTS])
+def test_pins_catch_a_planted_mistake(outcomes, name, pins):
+    r = outcomes[name]
     assert r.returncode == 1, f"{name}: pins {pins} did not fail (exit {r.returncode})\n{r.stdout[-3000:]}"

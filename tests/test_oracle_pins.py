@@ -466,6 +466,30 @@ def test_csf_force_on_cylinder_matches_continuum(lattice):
     assert np.all(np.sign(Fr[band]) == np.sign(cont[band]))
 
 
+def test_csf_acts_in_gray_cells_only_unless_everywhere():
+    """Eq. 4 is the under-resolved regions' surface-tension control: with
+    csf_everywhere = 0 its force is exactly zero in pore cells and, in gray
+    cells, equal to the force of the same densities with Eq. 4 applied
+    everywhere (it depends on the densities only)."""
+    n, R, w = 64, 20.0, 4.0
+    shape = (1, n, n)
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    r = np.sqrt((x - n / 2 + 0.5) ** 2 + (y - n / 2 + 0.5) ** 2)
+    rhoB = (0.5 + 0.45 * np.tanh((r - R) / w))[None]
+    rhoA = (0.6 - 0.2 * np.tanh((r - R) / w))[None]
+    cell = np.where(x < n // 2, synth.GRAY, synth.PORE).astype(np.uint8)[None]
+    phi = np.where(cell == synth.GRAY, 0.5, 1.0)
+    F = {}
+    for everywhere in (0, 1):
+        p = O.make_params(shape, kappa=-0.045, csf_everywhere=everywhere, lattice="d2q9")
+        o = _rest_state(p, cell, rhoA, rhoB, phi=phi)
+        F[everywhere] = np.stack([o.force_term(O.TERM_CSF, a) for a in range(2)])
+    gray = cell == synth.GRAY
+    assert np.all(F[0][..., ~gray] == 0.0)
+    np.testing.assert_array_equal(F[0][..., gray], F[1][..., gray])
+    assert np.abs(F[1][..., ~gray]).max() > 1e-6  # the pore cells do carry a force when applied everywhere
+
+
 # --------------------------------------------------------------------------
 # Conservation
 # --------------------------------------------------------------------------
