@@ -82,6 +82,12 @@ MUTANTS = [
      "double kref = kozeny_carman(cv, phi);", "test_leverett_invariance_and_residual_crossings"),
     ("outlet_plane", "if (x == p->nx - 1) fout += u0;", "if (x == 0) fout += u0;",
      "test_observables_are_plain_sums"),
+    ("gradient_weight_dropped", "M[a][b] = acc + st->p.c_g * g[a] * g[b];", "M[a][b] = acc + g[a] * g[b];",
+     "test_principal_axis_on_cosine_porosity"),
+    ("hessian_cross_factor", "H[a][b] = H[b][a] = 0.25 * (pp - pm - mp + mm);",
+     "H[a][b] = H[b][a] = 0.5 * (pp - pm - mp + mm);", "test_principal_axis_on_cosine_porosity"),
+    ("kozeny_d_squared", "return cv->kc_d * cv->kc_d * phi * phi * phi", "return cv->kc_d * phi * phi * phi",
+     "test_two_component_darcy_with_corey_permeabilities"),
 ]
 
 

@@ -625,16 +625,18 @@ def test_tiny_porosity_wave_keeps_its_axis(delta):
     assert np.abs(st["kinv"][0, 1] * K0).max() < 1e-9
 
 
+@pytest.mark.parametrize("c_g", [1.0, 4.0])
 @pytest.mark.parametrize("m", [(1, 0, 0), (0, 1, 0), (1, 1, 0), (1, 1, 1), (1, 2, 3), (2, 0, 1)])
-def test_principal_axis_on_cosine_porosity(m):
-    """Closed-form Hessian and gradient of phi0 + a cos(k.x), eigh for e1."""
+def test_principal_axis_on_cosine_porosity(m, c_g):
+    """Closed-form Hessian and gradient of phi0 + a cos(k.x), eigh for e1 of
+    M = H H + c_g grad(phi) grad(phi)^T (two weights of the gradient term)."""
     n = 12
     shape = (n, n, n)
     k = 2 * np.pi * np.array(m, float) / n
     amp, phi0, aniso = 0.1, 0.4, 7.0
     phi = synth.cosine_porosity(shape, phi0, amp, k)
     cell = np.full(shape, synth.GRAY, np.uint8)
-    o = O.Oracle(O.make_params(shape), cell, phi, curves=[O.make_curve(aniso=aniso)])
+    o = O.Oracle(O.make_params(shape, c_g=c_g), cell, phi, curves=[O.make_curve(aniso=aniso)])
     st = o.static()
     Mk = cosine_hessian_matrix(k)
     v = stencil_sine_vector(k) / CS2
@@ -644,7 +646,7 @@ def test_principal_axis_on_cosine_porosity(m):
     for idx in zip(*[a.ravel() for a in (z, y, x)]):
         H = -amp * np.cos(th[idx]) * Mk
         g = -amp * np.sin(th[idx]) * v
-        M = H @ H + np.outer(g, g)
+        M = H @ H + c_g * np.outer(g, g)
         wv, V = np.linalg.eigh(M)
         K0 = kc(phi[idx])
         got = st["kinv"][(slice(None), slice(None)) + idx]
