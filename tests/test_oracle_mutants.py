@@ -121,10 +121,12 @@ def outcomes(tmp_path_factory):
     for name, old, new, pins in MUTANTS:
         assert text.count(old) == 1, f"{name}: the mutated text must occur exactly once"
         jobs.append((name, text.replace(old, new), pins))
+    # the directories first, in this thread (tmp_path_factory is not thread-safe)
+    dirs = {name: tmp_path_factory.mktemp(name) for name, _, _ in jobs}
 
     def run(job):
         name, variant, pins = job
-        return name, _run_pins(_build(tmp_path_factory.mktemp(name), variant), pins)
+        return name, _run_pins(_build(dirs[name], variant), pins)
 
     workers = max(1, min(8, (os.cpu_count() or 2) // 2))
     with ThreadPoolExecutor(max_workers=workers) as ex:
