@@ -88,6 +88,8 @@ MUTANTS = [
      "H[a][b] = H[b][a] = 0.5 * (pp - pm - mp + mm);", "test_principal_axis_on_cosine_porosity"),
     ("kozeny_d_squared", "return cv->kc_d * cv->kc_d * phi * phi * phi", "return cv->kc_d * phi * phi * phi",
      "test_two_component_darcy_with_corey_permeabilities"),
+    ("probe_inside_outside", "if (r2 < probe[3] * probe[3]) { pin += pr; nin += 1; }",
+     "if (r2 > probe[3] * probe[3]) { pin += pr; nin += 1; }", "test_observables_are_plain_sums"),
 ]
 
 

@@ -866,6 +866,14 @@ def test_observables_are_plain_sums(pressure):
     assert abs(ob["sat"] - (phic * sw)[inner].sum() / phic[inner].sum()) < 1e-13
     assert abs(ob["flux_out"] - u[0, :, :, -1].sum() / 64) < 1e-15
     assert abs(ob["max_u"] - np.sqrt((u ** 2).sum(axis=0))[fl].max()) < 1e-15
+    # the probe: mean mixture pressure within r_in of the centre minus the mean
+    # beyond r_out, over fluid cells (the reservoirs included)
+    zz, yy, xx = np.meshgrid(*(np.arange(k) for k in cell.shape), indexing="ij")
+    r2 = (xx - 4) ** 2 + (yy - 4) ** 2 + (zz - 4) ** 2
+    pr = (a + b) / 3.0 + o.params.G * a * b
+    inside, outside = fl & (r2 < 2.5 ** 2), fl & (r2 > 3.5 ** 2)
+    assert inside.any() and outside.any()
+    assert abs(ob["dp"] - (pr[inside].mean() - pr[outside].mean())) < 1e-14
 
 
 # --------------------------------------------------------------------------
