@@ -7,7 +7,8 @@ mutant with gcc, and runs in a fresh process the pins of
 pointed at the mutant (several mutants at a time).  The pins must fail (pytest exit status 1: failures,
 not errors).  A control run of the same pins against the unchanged source
 must pass, so that the failures come from the mistakes and not from the
-harness.
+harness.  The PyTorch statement of the discrete adjoint (oracle/adjoint.py)
+gets the same treatment against its own pins.
 """
 import os
 import subprocess
@@ -144,3 +145,55 @@ def test_control_unchanged_oracle_passes_the_pins(outcomes):
 def test_pins_catch_a_planted_mistake(outcomes, name, pins):
     r = outcomes[name]
     assert r.returncode == 1, f"{name}: pins {pins} did not fail (exit {r.returncode})\n{r.stdout[-3000:]}"
+
+
+# ---- the discrete adjoint's PyTorch statement (oracle/adjoint.py) ----------
+ADJ_SRC = os.path.join(REPO, "oracle", "adjoint.py")
+ADJ_PINS = os.path.join(TESTS, "test_oracle_adjoint.py")
+ADJ_MUTANTS = [
+    ("eigen_gap_sign", "gap = w[..., 2] - w[..., k]", "gap = w[..., k] - w[..., 2]"),
+    ("eigen_direction_dropped", "for k in (0, 1):", "for k in (0,):"),
+    ("adjoint_kozeny_power", "return d * d * phi ** 3 / (180.0 * (1.0 - phi) ** 2)",
+     "return d * d * phi ** 3 / (180.0 * (1.0 - phi))"),
+]
+
+
+def _run_adjoint_pins(path):
+    code = (f"import sys; sys.path[:0] = [{REPO!r}, {TESTS!r}]\n"
+            "import importlib.util, oracle\n"
+            f"spec = importlib.util.spec_from_file_location('oracle.adjoint', {path!r})\n"
+            "mod = importlib.util.module_from_spec(spec); sys.modules['oracle.adjoint'] = mod\n"
+            "spec.loader.exec_module(mod); oracle.adjoint = mod\n"
+            "import pytest\n"
+            f"sys.exit(pytest.main(['-q', '-x', '-p', 'no:cacheprovider', {ADJ_PINS!r}]))\n")
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    return subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=900, cwd=REPO,
+                          env=env)
+
+
+@pytest.fixture(scope="module")
+def adjoint_outcomes(tmp_path_factory):
+    with open(ADJ_SRC) as f:
+        text = f.read()
+    jobs = [("control", text)]
+    for name, old, new in ADJ_MUTANTS:
+        assert text.count(old) == 1, f"{name}: the mutated text must occur exactly once"
+        jobs.append((name, text.replace(old, new)))
+    paths = {}
+    for name, variant in jobs:  # files first, in this thread
+        path = tmp_path_factory.mktemp("adj_" + name) / "adjoint.py"
+        path.write_text(variant)
+        paths[name] = str(path)
+    with ThreadPoolExecutor(max_workers=max(1, min(4, (os.cpu_count() or 2) // 2))) as ex:
+        return dict(zip([j[0] for j in jobs], ex.map(_run_adjoint_pins, [paths[j[0]] for j in jobs])))
+
+
+def test_control_unchanged_adjoint_statement_passes_its_pins(adjoint_outcomes):
+    r = adjoint_outcomes["control"]
+    assert r.returncode == 0, r.stdout[-3000:]
+
+
+@pytest.mark.parametrize("name", [m[0] for m in ADJ_MUTANTS])
+def test_adjoint_pins_catch_a_planted_mistake(adjoint_outcomes, name):
+    r = adjoint_outcomes[name]
+    assert r.returncode == 1, f"{name}: the adjoint pins did not fail (exit {r.returncode})\n{r.stdout[-3000:]}"
