@@ -91,6 +91,8 @@ MUTANTS = [
      "test_two_component_darcy_with_corey_permeabilities"),
     ("probe_inside_outside", "if (r2 < probe[3] * probe[3]) { pin += pr; nin += 1; }",
      "if (r2 > probe[3] * probe[3]) { pin += pr; nin += 1; }", "test_observables_are_plain_sums"),
+    ("mss_not_rest_equilibrium", "st->f[((long)a * Q + i) * n + c] = fout[i] + sgn * L->w[i] * dm;",
+     "st->f[((long)a * Q + i) * n + c] = fout[i] + sgn * dm / Q;", "test_mass_sink_source_special_cases"),
 ]
 
 

@@ -754,6 +754,12 @@ def test_mass_sink_source_special_cases(lattice):
         assert np.allclose(df.sum(axis=1)[1], moved, atol=1e-14) and np.allclose(df.sum(axis=1)[0], -moved, atol=1e-14)
         # every opposite pair gains the same amount (i odd and i + 1 are opposites in both sets)
         assert np.abs(df[:, 1::2] - df[:, 2::2]).max() < 1e-15
+        if moved:  # in every cell the added populations are w_i dm: the lattice's weights as a multiset
+            W = ([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12) if lattice == "d3q19" else ([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+            per_cell = df.reshape(2, df.shape[1], -1)
+            for c in range(per_cell.shape[2]):
+                np.testing.assert_allclose(np.sort(per_cell[1, :, c]) / moved, np.sort(W), rtol=1e-9)
+                np.testing.assert_allclose(np.sort(-per_cell[0, :, c]) / moved, np.sort(W), rtol=1e-9)
 
 
 def test_residual_hysteresis_switches():
