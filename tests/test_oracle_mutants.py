@@ -93,6 +93,13 @@ MUTANTS = [
      "if (r2 > probe[3] * probe[3]) { pin += pr; nin += 1; }", "test_observables_are_plain_sums"),
     ("mss_not_rest_equilibrium", "st->f[((long)a * Q + i) * n + c] = fout[i] + sgn * L->w[i] * dm;",
      "st->f[((long)a * Q + i) * n + c] = fout[i] + sgn * dm / Q;", "test_mass_sink_source_special_cases"),
+    ("curvature_normal_term_sign", "double div = (H[0][0] + H[1][1] + H[2][2]) / s - gHg / (s * s * s);",
+     "double div = (H[0][0] + H[1][1] + H[2][2]) / s + gHg / (s * s * s);",
+     "test_csf_force_on_cylinder_matches_continuum"),
+    ("hessian_trace_part", "(L->cv[i][d] * L->cv[i][e] - (d == e && d < L->dim ? CS2 : 0.0)) * df",
+     "(L->cv[i][d] * L->cv[i][e]) * df", "test_csf_force_on_cylinder_matches_continuum"),
+    ("hessian_identity_of_3d_in_2d", "(d == e && d < L->dim ? CS2 : 0.0)", "(d == e && d < 3 ? CS2 : 0.0)",
+     "test_csf_force_on_cylinder_matches_continuum"),
 ]
 
 
