@@ -67,7 +67,10 @@ def fiber_inputs(edge=192, axis=0):
 
 
 def algorithmic_bytes(cell):
-    """Bytes each kernel must move per launch (per-cell figures)."""
+    """Bytes each kernel must move per launch: 304 B per fluid cell (two
+    components x 19 FP32 populations, read and written), 1 B cell type per
+    cell and 25 B per gray cell (porosity, principal axis, residual state);
+    per-kernel figures count what each kernel itself reads."""
     n = cell.size
     fluid = int((cell != 1).sum())
     gray = int((cell == 2).sum())
@@ -76,6 +79,7 @@ def algorithmic_bytes(cell):
                 step_lp=fluid * 152 + n * 1 + gray * 25,
                 step_r16=fluid * 160 + n * 1 + gray * 25,
                 k_fused=fluid * 304 + n * 1 + gray * 32,
+                k_march=fluid * 304 + n * 1 + gray * 25,
                 k_fused_lp=fluid * 152 + n * 1 + gray * 32,
                 k_collide=fluid * 304 + n * 1 + n * 8 + gray * 32,
                 k_density=fluid * 152 + n * 1 + n * 8), fluid, gray
@@ -990,7 +994,8 @@ def main():
                          "every two-phase run to its target Sw with the mass-sink-source controller, then to steady "
                          "flow, before the timed steps (at most this many steps each)")
     ap.add_argument("--tile", type=int, default=2,
-                    help="fused tile: 0 = 32x8, 1 = 32x16, 2 = 32x8 two CTAs/SM, 3 = 32x12, 4 = 64x8")
+                    help="fused tile: 0 = 32x8, 1 = 32x16, 2 = 32x8 two CTAs/SM, 3 = 32x12, 4 = 64x8, "
+                         "5 / 6 = published-density march 32x8 / 32x7")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

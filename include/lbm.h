@@ -346,10 +346,26 @@ LBM_API int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *c
 /* Kernel path of lbm_step: path 0 (default) = one fused launch per step
  * (rolling z-window with shared-memory halos), path 1 = two launches
  * (densities, then forces + collision).  tile selects the fused tile:
- * 0 = 32x8 columns, 1 = 32x16, 2 = 32x8 with two CTAs per SM (the default),
- * 3 = 32x12, 4 = 64x8.  Both paths and all tiles compute identical states.
- * LBM_ERR_ARG on unknown values. */
+ * 0 = 32x8 columns, 1 = 32x16, 2 = 32x8 with two CTAs per SM, 3 = 32x12,
+ * 4 = 64x8, 5 and 6 = the published-density march on 32x8 and 32x7 tiles
+ * (every CTA resident, one cooperative launch per step: each tile publishes
+ * its densities and reads its ring from its neighbours instead of
+ * recomputing it; no CUDA-graph replay).  The march runs the plain F32 step;
+ * with reservoir cells, a mass-sink-source rate, a 16-bit storage or more
+ * tile columns than resident CTAs, tiles 5 and 6 run tile 2.  Default: 2.
+ * Both paths and all tiles compute
+ * identical states.  A march whose bounded wait for a neighbouring tile gave
+ * up (1 s) makes the next lbm_observables or lbm_get_fields return
+ * LBM_ERR_TIMEOUT.  LBM_ERR_ARG on unknown values. */
 LBM_API int lbm_set_kernel(lbm_ctx *ctx, int path, int tile);
+
+/* Testing hook for the error path of lbm_step (no counterpart in the paper):
+ * the next count step launches are issued with a zero-size thread block, a
+ * configuration the CUDA runtime rejects on the host before any device work.
+ * lbm_step then returns LBM_ERR_CUDA and the context keeps the state of the
+ * last step that ran (buffer parity, step count, fields).  count = 0 cancels.
+ * LBM_ERR_ARG on a NULL context or a negative count.  No device work. */
+LBM_API int lbm_inject_launch_failures(lbm_ctx *ctx, int count);
 
 /* ---- Porosity gradient (discrete adjoint) ---------------------------------
  * Loss on the fields of the last step (outlet flux and saturation mismatch):
@@ -454,13 +470,17 @@ LBM_API int lbm_launch_count(lbm_ctx *ctx, long long *count);
  * on `stream` (cudaStream_t, NULL = legacy default), and writes *out (host;
  * out->step is 0).  Synchronises the stream.
  * Scratch: a file-scope device array of 77,952 bytes that every GPU loading
- * this library holds until exit.  The first call on a device resolves that
- * array's address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * race.  Nothing is allocated, freed, or needs clearing between calls.
+ * this library holds until exit.  Every call resolves that array's address
+ * in the context current to the calling thread (cudaGetSymbolAddress: the
+ * device's primary context, a context the caller made current, a primary
+ * context re-created after cudaDeviceReset).  All calls share the array:
+ * calls that overlap on the GPU race.  Nothing is
+ * allocated, freed, or needs clearing between calls.  The call synchronises
+ * its stream and so cannot be captured into a CUDA graph.
  * Errors: LBM_ERR_ARG for NULL pointers, sizes < 1 or more than
- * LBM_NOALLOC_MAX_CELLS cells; LBM_ERR_CUDA; LBM_ERR_NUMERIC when non-finite
- * values were found (out is still filled). */
+ * LBM_NOALLOC_MAX_CELLS cells, or a stream that is being captured (checked
+ * before any work); LBM_ERR_CUDA; LBM_ERR_NUMERIC when non-finite values were
+ * found (out is still filled). */
 #define LBM_NOALLOC_MAX_CELLS (1LL << 28)
 LBM_API int lbm_observables_noalloc(const float *fields, const uint8_t *type, const float *phi, int nx, int ny,
                                     int nz, double G, const double probe[5], void *stream, lbm_obs *out);

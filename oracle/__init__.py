@@ -46,6 +46,7 @@ class OrcParams(C.Structure):
         ("rho_in", C.c_double * 2), ("rho_out", C.c_double * 2),
         ("lattice", C.c_int),
         ("mss", C.c_double),
+        ("csf_div", C.c_int),
     ]
 
 
@@ -85,6 +86,7 @@ def _load():
         lib.orc_force_term.argtypes = [P, C.c_int, C.c_int, dp]
         lib.orc_static.argtypes = [P, dp, dp, dp, dp, dp, ip]
         lib.orc_observables.argtypes = [P, dp, dp]
+        lib.orc_observables_of.argtypes = [C.c_int, C.c_int, C.c_int, u8, dp, dp, dp, dp, dp, C.c_double, dp, dp]
         lib.orc_set_populations.argtypes = [P, dp]
         lib.orc_set_pressure.argtypes = [P, dp, dp]
         lib.orc_set_mss.argtypes = [P, C.c_double]
@@ -117,6 +119,18 @@ def collide_cell(f, u, F, tau):
                              np.ascontiguousarray(u, dtype=np.float64),
                              np.ascontiguousarray(F, dtype=np.float64), float(tau), out)
     return out
+
+
+def observables_of(cell, phi, rhoA, rhoB, u, sw, G, probe=(0.0, 0.0, 0.0, 0.0, 1e30)):
+    """Observables (the definitions of Oracle.observables) of given fields on a
+    grid of shape (nz, ny, nx); u has shape (3, nz, ny, nx).  FP64."""
+    nz, ny, nx = np.shape(cell)
+    out = np.zeros(10)
+    f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    _load().orc_observables_of(nx, ny, nz, np.ascontiguousarray(cell, np.uint8).reshape(-1), f64(phi), f64(rhoA),
+                               f64(rhoB), f64(u), f64(sw), float(G), np.asarray(probe, dtype=np.float64), out)
+    return dict(mass=(out[0], out[1]), sat=out[2], flux_out=out[3], flux_vol=(out[4], out[5], out[6]),
+                max_u=out[7], dp=out[8], nan_count=int(out[9]))
 
 
 def make_params(shape, **kw) -> OrcParams:
@@ -154,6 +168,7 @@ def make_params(shape, **kw) -> OrcParams:
     p.c_g = kw.pop("c_g", 1.0)
     p.lattice = {"d3q19": 0, "d2q9": 1}[kw.pop("lattice", "d3q19")]
     p.mss = kw.pop("mss", 0.0)
+    p.csf_div = {"identity": 0, "neighbour_normals": 1}[kw.pop("csf_div", "identity")]
     rin = kw.pop("rho_in", (rho_hi, rho_lo))
     rout = kw.pop("rho_out", (rho_hi, rho_lo))
     for a in range(2):

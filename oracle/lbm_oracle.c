@@ -26,7 +26,11 @@
  *     and the regularised normal n = g / s, s = sqrt(|g|^2 + eps_n^2),
  *     div n = tr(H)/s - g.H.g / s^3 (curvature identity), evaluated with the
  *     isotropic D3Q19 gradient and the D3Q19 moment Hessian of the cell's own
- *     neighbourhood (solid neighbours carry rho_wall).
+ *     neighbourhood (solid neighbours carry rho_wall).  The other reading,
+ *     selectable for the pins that bound the choice (csf_div = 1), is the
+ *     isotropic divergence (1/cs^2) sum_i w_i n(x + c_i) . c_i of the unit
+ *     normals n = g / max(|g|, eps_n) at the neighbours (zero at solid
+ *     neighbours and outside).
  *   - Multiscale force of Eq. 1 in gray cells: capillary term
  *     -Pc(Sw) rho_r n H and the viscous resistance, the latter made tensorial
  *     by Eqs. 6-7 (principal axis from the Hessian and gradient of porosity,
@@ -107,6 +111,7 @@ typedef struct {
     double rho_in[2], rho_out[2]; /* densities held in inlet / outlet cells */
     int lattice;                  /* 0: D3Q19; 1: D2Q9 (nz = 1) */
     double mss;                   /* mass-sink-source rate m (0: off) */
+    int csf_div;                  /* Eq. 4 divergence: 0 curvature identity, 1 neighbour normals */
 } orc_params;
 
 typedef struct {
@@ -745,14 +750,30 @@ static void one_step(orc_state *st)
             if (p->kappa != 0.0 && (p->csf_everywhere || gray)) {
                 /* Eq. 4: kappa (-div n^a) (grad phi^a / phi_avg) (rho^a / phi_max),
                  * div n = tr(H)/s - g.H.g/s^3, s = sqrt(|g|^2 + eps_n^2) */
-                double H[3][3], g[3];
-                density_hessian(st, c, 1 - a, H);
-                for (int d = 0; d < 3; ++d) g[d] = st->grad[a][d * n + c];
-                double s = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2] + p->eps_n * p->eps_n);
-                double gHg = 0.0;
-                for (int d = 0; d < 3; ++d)
-                    for (int e = 0; e < 3; ++e) gHg += g[d] * H[d][e] * g[e];
-                double div = (H[0][0] + H[1][1] + H[2][2]) / s - gHg / (s * s * s);
+                double div = 0.0;
+                if (p->csf_div == 1) {
+                    /* divergence of the neighbours' unit normals g / max(|g|, eps_n) */
+                    for (int i = 1; i < Q; ++i) {
+                        long m = neighbour(st, c, L->cv[i][0], L->cv[i][1], L->cv[i][2]);
+                        if (m < 0) continue;
+                        double gm[3], mag2 = 0.0;
+                        for (int d = 0; d < 3; ++d) {
+                            gm[d] = st->grad[a][d * n + m];
+                            mag2 += gm[d] * gm[d];
+                        }
+                        double den = fmax(sqrt(mag2), p->eps_n);
+                        for (int d = 0; d < 3; ++d) div += L->w[i] * (gm[d] / den) * L->cv[i][d] / CS2;
+                    }
+                } else {
+                    double H[3][3], g[3];
+                    density_hessian(st, c, 1 - a, H);
+                    for (int d = 0; d < 3; ++d) g[d] = st->grad[a][d * n + c];
+                    double s = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2] + p->eps_n * p->eps_n);
+                    double gHg = 0.0;
+                    for (int d = 0; d < 3; ++d)
+                        for (int e = 0; e < 3; ++e) gHg += g[d] * H[d][e] * g[e];
+                    div = (H[0][0] + H[1][1] + H[2][2]) / s - gHg / (s * s * s);
+                }
                 for (int d = 0; d < 3; ++d)
                     T[T_CSF][a][d] = p->kappa * (-div) * (st->grad[a][d * n + c] / p->phi_avg[a]) *
                                      (r[a] / p->phi_max[a]);
@@ -901,54 +922,62 @@ void orc_static(const orc_state *st, double *kinv, double *K0, double *lamL, dou
     memcpy(iso, st->iso, sizeof(int) * (size_t)n);
 }
 
-/* Observables: out[0..1] mass of A and B; out[2] saturation
+/* Observables (S8) of fields given as arrays over an nx x ny x nz grid
+ * (x fastest): out[0..1] mass of A and B; out[2] saturation
  * sum(phi_c Sw)/sum(phi_c) (phi_c = 1 in pore, phi in gray, pressure cells
- * left out); out[3] mean
- * u_x over the outlet plane x = nx-1; out[4..6] volume mean of u; out[7]
- * max |u|; out[8] mean pressure inside radius r_in minus outside r_out about
- * the probe centre, p = cs^2 (rhoA+rhoB) + G rhoA rhoB; out[9] count of
- * non-finite density or velocity values.  probe = {cx, cy, cz, r_in, r_out}. */
-void orc_observables(const orc_state *st, const double probe[5], double out[10])
+ * left out); out[3] mean u_x over the outlet plane x = nx-1; out[4..6] volume
+ * mean of u; out[7] max |u|; out[8] mean pressure inside radius r_in minus
+ * outside r_out about the probe centre, p = cs^2 (rhoA+rhoB) + G rhoA rhoB;
+ * out[9] count of non-finite density or velocity values (such cells are left
+ * out of every sum).  probe = {cx, cy, cz, r_in, r_out}; u is [3][n]. */
+void orc_observables_of(int nx, int ny, int nz, const unsigned char *type, const double *phi, const double *rhoA,
+                        const double *rhoB, const double *u, const double *sw, double G, const double probe[5],
+                        double out[10])
 {
-    long n = st->n;
-    const orc_params *p = &st->p;
+    long n = (long)nx * ny * nz;
     double mass[2] = {0, 0}, satn = 0, satd = 0, fout = 0, fv[3] = {0, 0, 0}, umax = 0;
     double pin = 0, nin = 0, pout = 0, nout = 0, bad = 0;
     for (long c = 0; c < n; ++c) {
-        if (st->type[c] == SOLID) continue;
-        int x, y, z;
-        cell_coords(st, c, &x, &y, &z);
-        double ra = st->rho[0][c], rb = st->rho[1][c];
-        double u0 = st->u[c], u1 = st->u[n + c], u2 = st->u[2 * n + c];
+        if (type[c] == SOLID) continue;
+        int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
+        double ra = rhoA[c], rb = rhoB[c];
+        double u0 = u[c], u1 = u[n + c], u2 = u[2 * n + c];
         if (!isfinite(ra) || !isfinite(rb) || !isfinite(u0) || !isfinite(u1) || !isfinite(u2)) {
             bad += 1;
             continue;
         }
         mass[0] += ra;
         mass[1] += rb;
-        if (!is_pressure(st, c)) {
-            double phc = st->type[c] == GRAY ? st->phi[c] : 1.0;
-            satn += phc * st->sw[c];
+        if (type[c] != INLET && type[c] != OUTLET) {
+            double phc = type[c] == GRAY ? phi[c] : 1.0;
+            satn += phc * sw[c];
             satd += phc;
         }
-        if (x == p->nx - 1) fout += u0;
+        if (x == nx - 1) fout += u0;
         fv[0] += u0; fv[1] += u1; fv[2] += u2;
         double um = sqrt(u0 * u0 + u1 * u1 + u2 * u2);
         if (um > umax) umax = um;
         double dx = x - probe[0], dy = y - probe[1], dz = z - probe[2];
         double r2 = dx * dx + dy * dy + dz * dz;
-        double pr = CS2 * (ra + rb) + p->G * ra * rb;
+        double pr = CS2 * (ra + rb) + G * ra * rb;
         if (r2 < probe[3] * probe[3]) { pin += pr; nin += 1; }
         if (r2 > probe[4] * probe[4]) { pout += pr; nout += 1; }
     }
     out[0] = mass[0];
     out[1] = mass[1];
     out[2] = satd > 0 ? satn / satd : 0.0;
-    out[3] = fout / ((double)p->ny * p->nz);
+    out[3] = fout / ((double)ny * nz);
     for (int d = 0; d < 3; ++d) out[4 + d] = fv[d] / (double)n;
     out[7] = umax;
     out[8] = (nin > 0 ? pin / nin : 0.0) - (nout > 0 ? pout / nout : 0.0);
     out[9] = bad;
+}
+
+/* The observables of the oracle's own fields. */
+void orc_observables(const orc_state *st, const double probe[5], double out[10])
+{
+    orc_observables_of(st->p.nx, st->p.ny, st->p.nz, st->type, st->phi, st->rho[0], st->rho[1], st->u, st->sw,
+                       st->p.G, probe, out);
 }
 
 long orc_steps(const orc_state *st) { return st->steps; }

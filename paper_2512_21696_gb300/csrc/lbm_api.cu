@@ -300,6 +300,14 @@ int lbm_create(lbm_ctx **out, const lbm_params *p)
     if (e == cudaSuccess) e = cudaMalloc(&ctx->red, (size_t)(ctx->red_blocks + 1) * lbm::NOBS_HOST * sizeof(double));
     // zero: the reduction's completion count starts there
     if (e == cudaSuccess) e = cudaMemset(ctx->red, 0, (size_t)(ctx->red_blocks + 1) * lbm::NOBS_HOST * sizeof(double));
+    // the published-density march: wall masks, published densities, progress counters (zero)
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->wmask, N * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->pub, N * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemset(ctx->pub, 0, N * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->prog, lbm::MARCH_PROG_LEN * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(ctx->prog, 0, lbm::MARCH_PROG_LEN * sizeof(unsigned));
+    if (e == cudaSuccess) ctx->prog_len = lbm::MARCH_PROG_LEN;
+
     if (e != cudaSuccess) {
         int code = cuda_fail(e, "lbm_create allocation");
         lbm_destroy(ctx);
@@ -328,6 +336,9 @@ int lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->rho);
     cudaFree(ctx->macro);
     cudaFree(ctx->red);
+    cudaFree(ctx->wmask);
+    cudaFree(ctx->pub);
+    cudaFree(ctx->prog);
     delete ctx;
     return LBM_OK;
 }
@@ -386,6 +397,7 @@ int lbm_set_geometry(lbm_ctx *ctx, const uint8_t *type, const float *phi, const 
     LBM_CUDA(cudaMemsetAsync(ctx->gray, 0, N * sizeof(lbm::GrayRec), ctx->stream));
     fill_device_params(ctx);
     LBM_CUDA(lbm::launch_geometry(ctx, dpt));
+    LBM_CUDA(lbm::launch_wallmask(ctx));
     LBM_CUDA(cudaStreamSynchronize(ctx->stream));
     ctx->has_geometry = true;
     ctx->has_fields = false;
@@ -573,8 +585,9 @@ int lbm_step(lbm_ctx *ctx, int nsteps)
     // more than GRAPH_STEPS steps remain; the last steps, which write the
     // fields, run directly.  A caller capturing its own stream gets direct
     // launches (a capture of ours inside theirs could invalidate it).
+    // The march (tiles 5, 6) is a cooperative launch and steps directly.
     bool replay = !ctx->view && !ctx->profiling && !ctx->graph_off && ctx->n <= lbm::GRAPH_MAX_CELLS &&
-                  nsteps > lbm::GRAPH_STEPS + 1;
+                  ctx->tile != 5 && ctx->tile != 6 && nsteps > lbm::GRAPH_STEPS + 1;
     if (replay) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) {
@@ -610,6 +623,9 @@ int lbm_observables(lbm_ctx *ctx, lbm_obs *out)
     double v[LBM_OBS_RAW];
     LBM_CUDA(lbm::launch_observables(ctx, v));
     v[lbm::NOBS_HOST] = (double)ctx->steps;
+    int timed_out = 0;
+    LBM_CUDA(lbm::march_take_error(ctx, &timed_out));
+    if (timed_out) return LBM_ERR_TIMEOUT;
     return lbm_obs_decode(ctx, v, out);
 }
 
@@ -654,6 +670,9 @@ int lbm_get_fields(lbm_ctx *ctx, float *rhoA, float *rhoB, float *u, float *sw, 
     if (u) LBM_CUDA(cudaMemcpyAsync(u, ctx->macro + 2 * N, 3 * N * sizeof(float), kind, ctx->stream));
     if (sw) LBM_CUDA(cudaMemcpyAsync(sw, ctx->macro + 5 * N, N * sizeof(float), kind, ctx->stream));
     if (mem == LBM_MEM_HOST) LBM_CUDA(cudaStreamSynchronize(ctx->stream));
+    int timed_out = 0;
+    LBM_CUDA(lbm::march_take_error(ctx, &timed_out));
+    if (timed_out) return LBM_ERR_TIMEOUT;
     return LBM_OK;
 }
 
@@ -785,10 +804,18 @@ int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *count)
 
 int lbm_set_kernel(lbm_ctx *ctx, int path, int tile)
 {
-    if (!ctx || path < 0 || path > 1 || tile < 0 || tile > 4) return LBM_ERR_ARG;
+    if (!ctx || path < 0 || path > 1 || tile < 0 || tile > 7) return LBM_ERR_ARG;
     ctx->path = path;
     ctx->tile = tile;
     lbm::drop_graphs(ctx);
+    return LBM_OK;
+}
+
+int lbm_inject_launch_failures(lbm_ctx *ctx, int count)
+{
+    if (!ctx || count < 0) return LBM_ERR_ARG;
+    ctx->fail_launches = count;
+    lbm::drop_graphs(ctx);  // replays would bypass the launchers
     return LBM_OK;
 }
 

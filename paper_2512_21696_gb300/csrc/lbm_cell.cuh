@@ -464,14 +464,17 @@ struct StoreRest {
 //   csf  whether Eq. 4 applies here; hA, hB the Hessian sums of rho^A, rho^B.
 //   tgt  tgt(i): offset within a component's array where direction i goes,
 //        i n + (index of x + c_i), or opp(i) n + c when x + c_i is solid.
+//   ga, gb the cell's gray record (read by the caller, so that the load can be
+//        issued early; only used in gray cells), gray the array it came from
+//        (the residual flag is written back there on a transition).
 template <bool MACRO, class Store, class Target>
-__device__ __forceinline__ void collide_store(const DevParams &P, const float (&acc)[2][3], float mss, uint8_t t,
-                                              int c, int n,
-                                              Store &st,
-                                              const CompMom M[2], const float gf[2][3], const float gAt[3],
-                                              bool csf, const HessSum &hA, const HessSum &hB,
-                                              GrayRec *__restrict__ gray, float *__restrict__ macro,
-                                              const Target &tgt)
+__device__ __forceinline__ void collide_store_g(const DevParams &P, const float (&acc)[2][3], float mss, uint8_t t,
+                                                int c, int n,
+                                                Store &st,
+                                                const CompMom M[2], const float gf[2][3], const float gAt[3],
+                                                bool csf, const HessSum &hA, const HessSum &hB, const float4 ga,
+                                                const float4 gb, GrayRec *__restrict__ gray,
+                                                float *__restrict__ macro, const Target &tgt)
 {
     const float r[2] = {M[0].rho.hi, M[1].rho.hi};
     const float rt = r[0] + r[1];
@@ -532,8 +535,6 @@ __device__ __forceinline__ void collide_store(const DevParams &P, const float (&
     float sw = s;
     float u[3];
     if (is_gray) {
-        const float4 ga = gray[c].a;
-        const float4 gb = gray[c].b;
         unsigned meta = __float_as_uint(gb.w);
         bool wetf = meta & META_WET;
         bool swd = meta & META_SWITCHED;
@@ -664,6 +665,24 @@ __device__ __forceinline__ void collide_store(const DevParams &P, const float (&
         macro[(size_t)4 * n + c] = u[2];
         macro[(size_t)5 * n + c] = sw;
     }
+}
+
+// The same with the gray record read here.
+template <bool MACRO, class Store, class Target>
+__device__ __forceinline__ void collide_store(const DevParams &P, const float (&acc)[2][3], float mss, uint8_t t,
+                                              int c, int n,
+                                              Store &st,
+                                              const CompMom M[2], const float gf[2][3], const float gAt[3],
+                                              bool csf, const HessSum &hA, const HessSum &hB,
+                                              GrayRec *__restrict__ gray, float *__restrict__ macro,
+                                              const Target &tgt)
+{
+    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
+    if (t == CELL_GRAY) {
+        ga = gray[c].a;
+        gb = gray[c].b;
+    }
+    collide_store_g<MACRO>(P, acc, mss, t, c, n, st, M, gf, gAt, csf, hA, hB, ga, gb, gray, macro, tgt);
 }
 
 }  // namespace lbm

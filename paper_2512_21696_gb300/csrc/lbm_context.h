@@ -33,9 +33,14 @@ struct lbm_ctx {
     float *macro = nullptr;            // [6][n] rhoA, rhoB, ux, uy, uz, Sw
     double *red = nullptr;             // reduction partials
     int red_blocks = 0;
+    // published-density march (lbm_march.cu)
+    uint32_t *wmask = nullptr;         // [n] static wall mask: bits 1..18 neighbour solid/outside, 24..31 type
+    float2 *pub = nullptr;             // [n] densities (drho^A, drho^B) published during a step
+    unsigned *prog = nullptr;          // [prog_len] error flag, finished CTAs, progress per work item
+    int prog_len = 0;
 
     int path = 0;   // 0: fused single launch, 1: two launches (density, collide)
-    int tile = 2;   // fused tile variant (lbm_set_kernel); 2 = 32x8, two CTAs per SM
+    int tile = 2;   // fused tile variant (lbm_set_kernel); 2 = 32x8, two CTAs per SM; 5, 6 = the march
     bool has_geometry = false;
     bool has_fields = false;
     bool view = false;  // a run of a batch: buffers owned by the batch
@@ -57,6 +62,8 @@ struct lbm_ctx {
     };
     bool profiling = false;
     std::vector<ProfRec> prof;
+
+    int fail_launches = 0;  // step launches still to be issued with an invalid shape (lbm_inject_launch_failures)
 };
 
 namespace lbm {
@@ -83,6 +90,12 @@ cudaError_t launch_init(lbm_ctx *ctx, const float *rhoA, const float *rhoB, cons
 cudaError_t launch_density(lbm_ctx *ctx);
 cudaError_t launch_collide(lbm_ctx *ctx, bool write_macro);
 cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro);
+// The published-density march (tiles 5 and 6); *ran false where it does not apply.
+cudaError_t launch_march(lbm_ctx *ctx, bool write_macro, bool *ran);
+cudaError_t launch_wallmask(lbm_ctx *ctx);
+// Reads and clears the march's wait-timeout flag (synchronises the stream).
+cudaError_t march_take_error(lbm_ctx *ctx, int *flag);
+constexpr int MARCH_PROG_LEN = 2 + 4096;  // error flag, finished count, work items
 cudaError_t launch_fused_lp(lbm_ctx *ctx, bool write_macro);
 cudaError_t launch_d2q9_init(lbm_ctx *ctx, const float *rhoA, const float *rhoB, const float *u);
 cudaError_t launch_d2q9_step(lbm_ctx *ctx, bool write_macro);
@@ -98,6 +111,19 @@ template <class LY>
 inline LY lay_r16(lbm_ctx *ctx, int bi, int bo)
 {
     return LY::make(ctx->f[bi], ctx->f[bo], ctx->n);
+}
+
+// Block shape of a step launch: threads, or a zero-size block (a
+// configuration the CUDA runtime rejects on the host, before any device work)
+// while lbm_inject_launch_failures has launches pending.  Every step launcher
+// checks the launch before it counts it or flips the buffer parity.
+inline dim3 step_block(lbm_ctx *ctx, int threads)
+{
+    if (ctx->fail_launches > 0) {
+        --ctx->fail_launches;
+        return dim3(0, 1, 1);
+    }
+    return dim3(threads, 1, 1);
 }
 
 // Profiling helpers used around launches.

@@ -471,19 +471,25 @@ cudaError_t launch_d2q9_step(lbm_ctx *ctx, bool write_macro)
     float *fout = ctx->f[1 - ctx->cur];
     cudaEvent_t e0;
     prof_begin(ctx, "k2_density", &e0);
-    d2::k2_density<<<grid256(ctx->n), 256, 0, ctx->stream>>>(ctx->dp, fin, ctx->type, ctx->rho);
+    d2::k2_density<<<grid256(ctx->n), step_block(ctx, 256), 0, ctx->stream>>>(ctx->dp, fin, ctx->type, ctx->rho);
     prof_end(ctx, "k2_density", e0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ctx->launches += 1;
     prof_begin(ctx, "k2_collide", &e0);
+    const dim3 blk = step_block(ctx, 256);
     if (write_macro)
-        d2::k2_collide<true><<<grid256(ctx->n), 256, 0, ctx->stream>>>(ctx->dp, fin, fout, ctx->type, ctx->rho,
+        d2::k2_collide<true><<<grid256(ctx->n), blk, 0, ctx->stream>>>(ctx->dp, fin, fout, ctx->type, ctx->rho,
                                                                       ctx->gray, ctx->macro);
     else
-        d2::k2_collide<false><<<grid256(ctx->n), 256, 0, ctx->stream>>>(ctx->dp, fin, fout, ctx->type, ctx->rho,
+        d2::k2_collide<false><<<grid256(ctx->n), blk, 0, ctx->stream>>>(ctx->dp, fin, fout, ctx->type, ctx->rho,
                                                                        ctx->gray, ctx->macro);
     prof_end(ctx, "k2_collide", e0);
-    ctx->launches += 2;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;  // nothing ran: the state stays in buffer cur
+    ctx->launches += 1;
     ctx->cur = 1 - ctx->cur;
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 }  // namespace lbm

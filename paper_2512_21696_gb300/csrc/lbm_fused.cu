@@ -5,6 +5,7 @@
 // same time and the halo reads hit lines their neighbours have just brought
 // into L2.  The march itself is fused_item (lbm_fused.cuh).
 #include <algorithm>
+#include <type_traits>
 
 #include "lbm_context.h"
 #include "lbm_fused.cuh"
@@ -14,7 +15,7 @@ namespace lbm {
 template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY>
 __global__ void __launch_bounds__(TX *TY, MINB)
     k_fused(DevParams P, int zchunks, LY ly, const uint8_t *__restrict__ type, GrayRec *__restrict__ gray,
-            float *__restrict__ macro)
+            float *__restrict__ macro, int pf)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geo G = geo_of(P);
@@ -26,7 +27,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
         const int zb = (int)((long long)P.nz * (chunk + 1) / zchunks);
         if (za >= zb) continue;
         fused_item<TX, TY, MACRO, EXT>(P, G, ly, type, gray, macro, (col % tiles_x) * TX, (col / tiles_x) * TY, za,
-                                        zb, smem_raw);
+                                        zb, smem_raw, pf);
     }
 }
 
@@ -56,11 +57,16 @@ static cudaError_t launch_fused_t(lbm_ctx *ctx, LY ly)
     const long long grid = std::min<long long>(ncol * zchunks, slots);
     cudaEvent_t e0;
     prof_begin(ctx, "k_fused", &e0);
-    kern<<<(unsigned)grid, TX * TY, smem, ctx->stream>>>(ctx->dp, zchunks, ly, ctx->type, ctx->gray, ctx->macro);
+    // bulk L2 prefetch of the population rows: F32 rows 16-byte aligned (tile 7 only, for now)
+    const int pf = (std::is_same<LY, LayF32>::value && ctx->p.nx % 4 == 0 && ctx->tile == 7) ? 1 : 0;
+    kern<<<(unsigned)grid, step_block(ctx, TX * TY), smem, ctx->stream>>>(ctx->dp, zchunks, ly, ctx->type,
+                                                                        ctx->gray, ctx->macro, pf);
     prof_end(ctx, "k_fused", e0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;  // nothing ran: the state stays in buffer cur
     ctx->launches += 1;
     ctx->cur = 1 - ctx->cur;
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 // Geometries with reservoir cells, or a mass-sink-source rate, run the
@@ -81,6 +87,11 @@ static cudaError_t launch_fused_tile(lbm_ctx *ctx, bool write_macro, LY ly)
 // The rest-referenced 16-bit layouts run the default tile.
 cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro)
 {
+    if (ctx->tile == 5 || ctx->tile == 6) {  // the published-density march where it applies, else tile 2
+        bool ran = false;
+        const cudaError_t e = launch_march(ctx, write_macro, &ran);
+        if (e != cudaSuccess || ran) return e;
+    }
     if (ctx->p.storage == LBM_STORAGE_F16R)
         return launch_fused_tile<32, 8, 2>(ctx, write_macro, lay_r16<LayF16R>(ctx, ctx->cur, 1 - ctx->cur));
     if (ctx->p.storage == LBM_STORAGE_BF16R)
@@ -91,6 +102,7 @@ cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro)
     case 2: return launch_fused_tile<32, 8, 2>(ctx, write_macro, ly);
     case 3: return launch_fused_tile<32, 12, 1>(ctx, write_macro, ly);
     case 4: return launch_fused_tile<64, 8, 1>(ctx, write_macro, ly);
+    case 7: return launch_fused_tile<32, 8, 2>(ctx, write_macro, ly);
     default: return launch_fused_tile<32, 8, 1>(ctx, write_macro, ly);
     }
 }

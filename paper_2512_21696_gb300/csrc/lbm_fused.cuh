@@ -19,6 +19,8 @@
 // (lbm_cell.cuh), so both give identical states.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_cell.cuh"
 
 namespace lbm {
@@ -60,11 +62,14 @@ __device__ __forceinline__ int ring3(int p) { return ((p % 3) + 3) % 3; }
 // physics P.  EXT compiles in the reservoir (inlet / outlet) cells and the
 // mass-sink-source term; without it neither is expected.  Ends with a block
 // barrier, so the rings can be reused at once.
+// pf != 0: the population rows are 16-byte aligned (F32, nx a multiple of 4)
+// and each plane's rows are brought into L2 two planes ahead of their
+// density pass, one bulk prefetch per row.
 template <int TX, int TY, bool MACRO, bool EXT, class LY>
 __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, const LY &ly,
                                            const uint8_t *__restrict__ type,
                                            GrayRec *__restrict__ gray, float *__restrict__ macro, int x0, int y0,
-                                           int za, int zb, unsigned char *smem_raw)
+                                           int za, int zb, unsigned char *smem_raw, int pf = 0)
 {
     using T = Tiles<TX, TY>;
     RawCell *raw = reinterpret_cast<RawCell *>(smem_raw);         // [3][RN]
@@ -92,6 +97,22 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
                 }
             }
             dst[e] = rc;
+        }
+    };
+
+    // ---- L2 prefetch of the tile's population rows at plane q ----
+    auto prefetch_plane = [&](int q) {
+        if constexpr (std::is_same<LY, LayF32>::value) {
+            if (!pf) return;
+            const int gz = wrap_coord(q, G.nz, P.per[2]);
+            if (gz < 0) return;
+            const unsigned bytes = 4u * (unsigned)min(TX, G.nx - x0);
+            for (int r = tid; r < 2 * Q * TY; r += T::NT) {
+                const int slot = r / TY, gy = y0 + r % TY;
+                if (gy >= G.ny) continue;
+                const float *row = ly.in + (size_t)slot * n + x0 + (size_t)G.nx * (gy + (size_t)G.ny * gz);
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(row), "r"(bytes) : "memory");
+            }
         }
     };
 
@@ -166,6 +187,11 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
             return;
         }
         const int c = me.gidx;
+        float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga;
+        if (me.type == CELL_GRAY) {  // issued first: used only after the pull and the stencils
+            ga = gray[c].a;
+            gb = gray[c].b;
+        }
         const DenCell dc = d1[dk];
         unsigned wall = 0;
 #pragma unroll
@@ -233,13 +259,15 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
                 if (held) gf[a][d] = 0.f;
             }
         StoreRest<LY> st{ly, c, {f0i[0], f0i[1]}};
-        collide_store<MACRO>(P, acc, (EXT && !held) ? G.mss : 0.f, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro,
-                             tgt);
+        collide_store_g<MACRO>(P, acc, (EXT && !held) ? G.mss : 0.f, t, c, n, st, M, gf, gAt, csf, hA, hB, ga, gb,
+                               gray, macro, tgt);
     };
 
     load_raw(za - 2);
     load_raw(za - 1);
+    prefetch_plane(za);
     for (int L = za - 1; L <= zb; ++L) {
+        if (L + 2 <= zb) prefetch_plane(L + 2);
         load_raw(L + 1);
         __syncthreads();
         densities(L);

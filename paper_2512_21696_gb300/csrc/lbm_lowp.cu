@@ -200,12 +200,14 @@ static cudaError_t launch_lp_t(lbm_ctx *ctx)
     E *fout = reinterpret_cast<E *>(ctx->f[1 - ctx->cur]);
     cudaEvent_t e0;
     prof_begin(ctx, "k_fused_lp", &e0);
-    kern<<<(unsigned)grid, TX * TY, smem, ctx->stream>>>(ctx->dp, zchunks, fin, fout, ctx->type, ctx->gray,
-                                                         ctx->macro);
+    kern<<<(unsigned)grid, step_block(ctx, TX * TY), smem, ctx->stream>>>(ctx->dp, zchunks, fin, fout, ctx->type,
+                                                                        ctx->gray, ctx->macro);
     prof_end(ctx, "k_fused_lp", e0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;  // nothing ran: the state stays in buffer cur
     ctx->launches += 1;
     ctx->cur = 1 - ctx->cur;
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 template <class H>

@@ -10,17 +10,20 @@
 //
 // The array is g_obs_scratch below: (OBS_MAX_BLOCKS + 1) * NOBS doubles =
 // 77,952 bytes, which every GPU that loads this library holds until the
-// process exits.  Its device address is resolved once per device with
-// cudaGetSymbolAddress by the first call on that device (host code must not
-// use the symbol itself: on the host it only names a stand-in).  Each call
-// overwrites every slot it later reads; the one slot that must start at zero,
-// the completion count in the final row, is zero at load and reset by each
-// call's last block.  Calls that overlap on the GPU (for example on two
-// streams) share the array and race.
-#include <atomic>
+// process exits.  Host code must not use the symbol itself (on the host it
+// only names a stand-in): every call resolves the array's device address in
+// the context current to the calling thread with cudaGetSymbolAddress (a
+// host-side lookup, small next to the synchronisation the call ends with), so
+// the device's primary context, a context the caller made current and a
+// primary context re-created after cudaDeviceReset each get the address of
+// their own copy of the module.  Each call overwrites every slot it later
+// reads; the one slot that must start at zero, the completion count in the
+// final row, is zero at load and reset by each call's last block.  Calls that
+// overlap on the GPU (for example on two streams) share the array and race.
+// The call synchronises its stream, so it cannot be captured into a CUDA
+// graph: on a capturing stream it returns LBM_ERR_ARG before any work.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "lbm_obs.cuh"
 
@@ -28,21 +31,13 @@ namespace {
 
 static __device__ __align__(256) double g_obs_scratch[(lbm::OBS_MAX_BLOCKS + 1) * lbm::NOBS];
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_scratch_mutex;
-double *g_scratch_ptr[MAX_DEVICES] = {};
-
-// Device address of g_obs_scratch on the current device (resolved once).
-cudaError_t scratch_address(int dev, double **out)
+// Device address of g_obs_scratch in the current context.
+cudaError_t scratch_address(double **out)
 {
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_obs_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_obs_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<double *>(p);
     return cudaSuccess;
 }
 
@@ -56,10 +51,12 @@ extern "C" LBM_API int lbm_observables_noalloc(const float *fields, const uint8_
     if (nx < 1 || ny < 1 || nz < 1) return LBM_ERR_ARG;
     const long long n = (long long)nx * ny * nz;
     if (n > LBM_NOALLOC_MAX_CELLS) return LBM_ERR_ARG;
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return LBM_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return LBM_ERR_ARG;  // the call synchronises: it cannot be captured
     double *scratch = nullptr;
-    if (scratch_address(dev, &scratch) != cudaSuccess) return LBM_ERR_CUDA;
+    if (scratch_address(&scratch) != cudaSuccess) return LBM_ERR_CUDA;
 
     lbm::DevParams P;
     std::memset(&P, 0, sizeof(P));
@@ -71,7 +68,6 @@ extern "C" LBM_API int lbm_observables_noalloc(const float *fields, const uint8_
     const int nb = lbm::obs_blocks((int)n);
     float2 *partial = reinterpret_cast<float2 *>(scratch);  // a float-float pair per double slot
     double *final_row = scratch + (size_t)lbm::OBS_MAX_BLOCKS * lbm::NOBS;
-    cudaStream_t s = (cudaStream_t)stream;
     lbm::k_obs_partial<<<nb, lbm::OBS_BLOCK, 0, s>>>(P, O, type, phi, fields, partial, final_row);
     if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
     double v[lbm::NOBS];

@@ -360,11 +360,13 @@ cudaError_t launch_density(lbm_ctx *ctx)
 {
     cudaEvent_t e0;
     prof_begin(ctx, "k_density", &e0);
-    k_density<<<grid_for(ctx->n, 256), 256, 0, ctx->stream>>>(ctx->dp, ctx->f[ctx->cur], ctx->type,
-                                                             ctx->rho);
+    k_density<<<grid_for(ctx->n, 256), step_block(ctx, 256), 0, ctx->stream>>>(ctx->dp, ctx->f[ctx->cur],
+                                                                              ctx->type, ctx->rho);
     prof_end(ctx, "k_density", e0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     ctx->launches += 1;
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 cudaError_t launch_collide(lbm_ctx *ctx, bool write_macro)
@@ -373,16 +375,19 @@ cudaError_t launch_collide(lbm_ctx *ctx, bool write_macro)
     float *fout = ctx->f[1 - ctx->cur];
     cudaEvent_t e0;
     prof_begin(ctx, "k_collide", &e0);
+    const dim3 blk = step_block(ctx, 256);
     if (write_macro)
-        k_collide<true><<<grid_for(ctx->n, 256), 256, 0, ctx->stream>>>(
+        k_collide<true><<<grid_for(ctx->n, 256), blk, 0, ctx->stream>>>(
             ctx->dp, fin, fout, ctx->type, ctx->rho, ctx->gray, ctx->macro);
     else
-        k_collide<false><<<grid_for(ctx->n, 256), 256, 0, ctx->stream>>>(
+        k_collide<false><<<grid_for(ctx->n, 256), blk, 0, ctx->stream>>>(
             ctx->dp, fin, fout, ctx->type, ctx->rho, ctx->gray, ctx->macro);
     prof_end(ctx, "k_collide", e0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;  // nothing ran: the state stays in buffer cur
     ctx->launches += 1;
     ctx->cur = 1 - ctx->cur;
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 }  // namespace lbm

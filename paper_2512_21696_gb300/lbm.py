@@ -315,8 +315,14 @@ def lbm_profile_read(ctx: LbmContext) -> dict:
 
 
 def lbm_set_kernel(ctx: LbmContext, path: int = 0, tile: int = 0) -> None:
-    """Kernel path of lbm_step: 0 fused (default), 1 two launches; fused tile 0 = 32x8, 1 = 32x16."""
+    """Kernel path of lbm_step: 0 fused (default), 1 two launches; fused tile 0 = 32x8, 1 = 32x16,
+    2 = 32x8 two CTAs per SM, 3 = 32x12, 4 = 64x8, 5 / 6 = the published-density march (32x8 / 32x7)."""
     _check(L.load().lbm_set_kernel(ctx.handle, int(path), int(tile)), "lbm_set_kernel")
+
+
+def lbm_inject_launch_failures(ctx: LbmContext, count: int) -> None:
+    """Testing hook: the next `count` step launches are rejected by the CUDA runtime on the host."""
+    _check(L.load().lbm_inject_launch_failures(ctx.handle, int(count)), "lbm_inject_launch_failures")
 
 
 def lbm_launch_count(ctx: LbmContext) -> int:

@@ -43,6 +43,19 @@ def rel_l2(a, b, mask=None):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def max_rel(a, b, mask=None):
+    """Element-wise error max|a - b| / max|b| (over the masked cells, all
+    components): the bound that a wrong value in a single cell cannot hide
+    under, where the L2 norm of a large lattice averages it away."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if mask is not None:
+        a = a[..., mask]
+        b = b[..., mask]
+    mb = np.abs(b).max() if b.size else 0.0
+    return float(np.abs(a - b).max() / (mb if mb > 0 else 1.0)) if b.size else 0.0
+
+
 def rest_only_populations(rhoA, rhoB, Q=19):
     """Post-collision state whose streamed densities equal (rhoA, rhoB) exactly.
 

@@ -57,7 +57,7 @@ MUTANTS = [
      "test_mass_sink_source_special_cases"),
     ("mss_background", "double I = (4.0 * rw * rn - Ib) / (1.0 - Ib);", "double I = (4.0 * rw * rn) / (1.0 - Ib);",
      "test_mass_sink_source_special_cases"),
-    ("saturation_weight", "double phc = st->type[c] == GRAY ? st->phi[c] : 1.0;", "double phc = 1.0;",
+    ("saturation_weight", "double phc = type[c] == GRAY ? phi[c] : 1.0;", "double phc = 1.0;",
      "test_observables_are_plain_sums"),
     ("capillary_sign", "T[T_CAP][a][d] = -Pc * (r[a] / rt)", "T[T_CAP][a][d] = Pc * (r[a] / rt)",
      "test_capillary_force_flat_interface_telescopes"),
@@ -81,7 +81,7 @@ MUTANTS = [
      "sw_at_pressure(cv, lamL, cv->f_min * pc_pm);", "test_leverett_invariance_and_residual_crossings"),
     ("leverett_reference_porosity", "double kref = kozeny_carman(cv, cv->phi_ref);",
      "double kref = kozeny_carman(cv, phi);", "test_leverett_invariance_and_residual_crossings"),
-    ("outlet_plane", "if (x == p->nx - 1) fout += u0;", "if (x == 0) fout += u0;",
+    ("outlet_plane", "if (x == nx - 1) fout += u0;", "if (x == 0) fout += u0;",
      "test_observables_are_plain_sums"),
     ("gradient_weight_dropped", "M[a][b] = acc + st->p.c_g * g[a] * g[b];", "M[a][b] = acc + g[a] * g[b];",
      "test_principal_axis_on_cosine_porosity"),
@@ -93,8 +93,8 @@ MUTANTS = [
      "if (r2 > probe[3] * probe[3]) { pin += pr; nin += 1; }", "test_observables_are_plain_sums"),
     ("mss_not_rest_equilibrium", "st->f[((long)a * Q + i) * n + c] = fout[i] + sgn * L->w[i] * dm;",
      "st->f[((long)a * Q + i) * n + c] = fout[i] + sgn * dm / Q;", "test_mass_sink_source_special_cases"),
-    ("curvature_normal_term_sign", "double div = (H[0][0] + H[1][1] + H[2][2]) / s - gHg / (s * s * s);",
-     "double div = (H[0][0] + H[1][1] + H[2][2]) / s + gHg / (s * s * s);",
+    ("curvature_normal_term_sign", "div = (H[0][0] + H[1][1] + H[2][2]) / s - gHg / (s * s * s);",
+     "div = (H[0][0] + H[1][1] + H[2][2]) / s + gHg / (s * s * s);",
      "test_csf_force_on_cylinder_matches_continuum"),
     ("hessian_trace_part", "(L->cv[i][d] * L->cv[i][e] - (d == e && d < L->dim ? CS2 : 0.0)) * df",
      "(L->cv[i][d] * L->cv[i][e]) * df", "test_csf_force_on_cylinder_matches_continuum"),
