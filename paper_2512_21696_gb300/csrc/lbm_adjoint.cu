@@ -10,10 +10,14 @@
 //                Eq. 3 force term, semi-implicit velocity (Sherman-Morrison),
 //                drag, capillary term, residual saturation, CSF curvature,
 //                Shan-Chen.  It writes the adjoint of its own arrived
-//                populations, adds the adjoints of the neighbour densities
-//                into acc (atomics) and accumulates the adjoints of its gray
-//                constants (v = sqrt(a-1) e1, 1/K0, lamL*pd, Sw_irr, So_res);
-//   k_adj_finish lam^n(y) = own part + acc(y) on every slot of y (rho = sum f).
+//                populations, the adjoints of its 18 neighbours' densities
+//                (one slot per direction, contrib[b][i][x]) and accumulates
+//                the adjoints of its gray constants (v = sqrt(a-1) e1, 1/K0,
+//                lamL*pd, Sw_irr, So_res);
+//   k_adj_finish lam^n(y) = own part + sum_i contrib[b][i][y - c_i] on every
+//                slot of y (rho = sum f): the adjoint of a push is a pull, so
+//                the neighbour terms are gathered in a fixed order (no
+//                atomics; the gradient does not depend on the scheduling).
 // After the last adjoint step k_geom_adjoint chains the gray constants to phi
 // (Kozeny-Carman, Leverett, the residual crossings and the principal axis,
 // d e1 = sum_{k != 1} e_k (e_k^T dM e1)/(mu1 - mu_k)), in FP64.
@@ -94,7 +98,8 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
                                                   const float *__restrict__ rhob, const uint8_t *__restrict__ type,
                                                   const float *__restrict__ phi, const GrayRec *__restrict__ gray,
                                                   const float *__restrict__ lam_next, float *__restrict__ lam_out,
-                                                  float *__restrict__ acc, double *__restrict__ gacc, AdjSeed seed)
+                                                  float *__restrict__ contrib, double *__restrict__ gacc,
+                                                  AdjSeed seed)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = P.n;
@@ -465,11 +470,13 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
             lam_out[(size_t)a * Q * n + (size_t)i * n + c] = v;
         }
     }
-    for (int i = 1; i < Q; ++i)
-        if (!(wall & (1u << i))) {
-            atomicAdd(&acc[nb[i]], lrn[0][i]);
-            atomicAdd(&acc[n + nb[i]], lrn[1][i]);
-        }
+    // the adjoint of neighbour x + c_i's density, read back by that neighbour
+    // (zero towards walls, which have no density)
+    for (int i = 1; i < Q; ++i) {
+        const bool wl = wall & (1u << i);
+        contrib[(size_t)i * n + c] = wl ? 0.f : lrn[0][i];
+        contrib[(size_t)(Q + i) * n + c] = wl ? 0.f : lrn[1][i];
+    }
     if (is_gray) {
         double *gk = gacc + (size_t)8 * c;
         gk[0] += (double)lv[0];
@@ -482,19 +489,33 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
     }
 }
 
-__global__ void k_adj_finish(int n, const uint8_t *__restrict__ type, float *__restrict__ lam,
-                             float *__restrict__ acc)
+__global__ void k_adj_finish(DevParams P, const uint8_t *__restrict__ type, float *__restrict__ lam,
+                             const float *__restrict__ contrib)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = P.n;
     if (c >= n) return;
     const bool solid = type[c] == CELL_SOLID;
+    const int x = c % P.nx, y = (c / P.nx) % P.ny, z = c / (P.nx * P.ny);
+    float v[2] = {0.f, 0.f};
+    if (!solid) {
+        // the fluid neighbours x - c_i that pushed into this cell along c_i
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int X = axis_nb(x, -cx(i), P.nx, P.per[0]), Y = axis_nb(y, -cy(i), P.ny, P.per[1]),
+                      Z = axis_nb(z, -cz(i), P.nz, P.per[2]);
+            if (X < 0 || Y < 0 || Z < 0) continue;
+            const int s = X + P.nx * (Y + P.ny * Z);
+            if (type[s] == CELL_SOLID) continue;
+            v[0] += contrib[(size_t)i * n + s];
+            v[1] += contrib[(size_t)(Q + i) * n + s];
+        }
+    }
     for (int a = 0; a < 2; ++a) {
-        const float v = acc[(size_t)a * n + c];
         for (int i = 0; i < Q; ++i) {
             float &l = lam[(size_t)a * Q * n + (size_t)i * n + c];
-            l = solid ? 0.f : l + v;
+            l = solid ? 0.f : l + v[a];
         }
-        acc[(size_t)a * n + c] = 0.f;
     }
 }
 
@@ -736,7 +757,7 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
     LBM_CUDA(cudaMalloc(&seg_g.p, gb * ckpt));
     LBM_CUDA(cudaMalloc(&lam0.p, pb));
     LBM_CUDA(cudaMalloc(&lam1.p, pb));
-    LBM_CUDA(cudaMalloc(&acc.p, 2 * (size_t)n * sizeof(float)));
+    LBM_CUDA(cudaMalloc(&acc.p, 2 * Q * (size_t)n * sizeof(float)));  // contrib[2][Q][n]
     LBM_CUDA(cudaMalloc(&gacc.p, 8 * (size_t)n * sizeof(double)));
     LBM_CUDA(cudaMalloc(&dphi.p, (size_t)n * sizeof(double)));
     LBM_CUDA(cudaMalloc(&fin_f.p, pb));
@@ -775,7 +796,7 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
     seed.lux = (float)(dLdq / ((double)ctx->p.ny * ctx->p.nz));
     seed.lsw = (float)(sumphi > 0 ? dLdS / sumphi : 0.0);
     LBM_CUDA(cudaMemsetAsync(lam0.p, 0, pb, s));
-    LBM_CUDA(cudaMemsetAsync(acc.p, 0, 2 * (size_t)n * sizeof(float), s));
+    LBM_CUDA(cudaMemsetAsync(acc.p, 0, 2 * Q * (size_t)n * sizeof(float), s));
     LBM_CUDA(cudaMemsetAsync(gacc.p, 0, 8 * (size_t)n * sizeof(double), s));
     LBM_CUDA(cudaMemsetAsync(dphi.p, 0, (size_t)n * sizeof(double), s));
     const dim3 grid((n + 127) / 128);
@@ -807,7 +828,7 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
             k_adj_cell<<<grid, 128, 0, s>>>(ctx->dp, ctx->f[0], ctx->rho, ctx->type, ctx->phi,
                                               (const GrayRec *)(sg + gb * (k - k0)), lam_next, lam_cur,
                                               (float *)acc.p, (double *)gacc.p, sk);
-            k_adj_finish<<<grid, 128, 0, s>>>(n, ctx->type, lam_cur, (float *)acc.p);
+            k_adj_finish<<<grid, 128, 0, s>>>(ctx->dp, ctx->type, lam_cur, (const float *)acc.p);
             e = cudaGetLastError();
             ctx->launches += 2;
             std::swap(lam_next, lam_cur);

@@ -290,7 +290,10 @@ int lbm_create(lbm_ctx **out, const lbm_params *p)
     fill_device_params(ctx);
     const size_t N = (size_t)n;
     cudaError_t e = cudaSuccess;
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc(&ctx->f[b], pop_bytes(ctx));
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaMalloc(&ctx->f[b], pop_bytes(ctx));
+        if (e == cudaSuccess) e = cudaMemset(ctx->f[b], 0, pop_bytes(ctx));  // solid cells' slots stay zero
+    }
     if (e == cudaSuccess) e = cudaMalloc(&ctx->type, N);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->phi, N * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->gray, N * sizeof(lbm::GrayRec));
@@ -804,7 +807,7 @@ int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *count)
 
 int lbm_set_kernel(lbm_ctx *ctx, int path, int tile)
 {
-    if (!ctx || path < 0 || path > 1 || tile < 0 || tile > 7) return LBM_ERR_ARG;
+    if (!ctx || path < 0 || path > 1 || tile < 0 || tile > 9) return LBM_ERR_ARG;
     ctx->path = path;
     ctx->tile = tile;
     lbm::drop_graphs(ctx);

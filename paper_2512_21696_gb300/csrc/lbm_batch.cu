@@ -404,7 +404,10 @@ int lbm_batch_create(lbm_batch **out, int nruns, const lbm_params *runs)
     b->tile_of_run.assign(nruns, 0);
     const size_t N = (size_t)b->cells;
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&b->f[k], b->pop_total);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&b->f[k], b->pop_total);
+        if (e == cudaSuccess) e = cudaMemset(b->f[k], 0, b->pop_total);  // solid cells' slots stay zero
+    }
     if (e == cudaSuccess) e = cudaMalloc(&b->type, N);
     if (e == cudaSuccess) e = cudaMalloc(&b->phi, N * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&b->gray, N * sizeof(lbm::GrayRec));

@@ -5,17 +5,16 @@
 // same time and the halo reads hit lines their neighbours have just brought
 // into L2.  The march itself is fused_item (lbm_fused.cuh).
 #include <algorithm>
-#include <type_traits>
 
 #include "lbm_context.h"
 #include "lbm_fused.cuh"
 
 namespace lbm {
 
-template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY>
+template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY, bool PF = false, bool ML = false>
 __global__ void __launch_bounds__(TX *TY, MINB)
     k_fused(DevParams P, int zchunks, LY ly, const uint8_t *__restrict__ type, GrayRec *__restrict__ gray,
-            float *__restrict__ macro, int pf)
+            float *__restrict__ macro)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geo G = geo_of(P);
@@ -26,16 +25,16 @@ __global__ void __launch_bounds__(TX *TY, MINB)
         const int za = (int)((long long)P.nz * chunk / zchunks);
         const int zb = (int)((long long)P.nz * (chunk + 1) / zchunks);
         if (za >= zb) continue;
-        fused_item<TX, TY, MACRO, EXT>(P, G, ly, type, gray, macro, (col % tiles_x) * TX, (col / tiles_x) * TY, za,
-                                        zb, smem_raw, pf);
+        fused_item<TX, TY, MACRO, EXT, LY, PF, ML>(P, G, ly, type, gray, macro, (col % tiles_x) * TX,
+                                                    (col / tiles_x) * TY, za, zb, smem_raw);
     }
 }
 
 // ---------------------------------------------------------------------------
-template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY>
+template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY, bool PF = false, bool ML = false>
 static cudaError_t launch_fused_t(lbm_ctx *ctx, LY ly)
 {
-    auto kern = k_fused<TX, TY, MINB, MACRO, EXT, LY>;
+    auto kern = k_fused<TX, TY, MINB, MACRO, EXT, LY, PF, ML>;
     const size_t smem = Tiles<TX, TY>::smem();
     // launch configuration, resolved once per device
     static int cached_slots[64] = {};  // resident CTAs per device
@@ -57,10 +56,8 @@ static cudaError_t launch_fused_t(lbm_ctx *ctx, LY ly)
     const long long grid = std::min<long long>(ncol * zchunks, slots);
     cudaEvent_t e0;
     prof_begin(ctx, "k_fused", &e0);
-    // bulk L2 prefetch of the population rows: F32 rows 16-byte aligned (tile 7 only, for now)
-    const int pf = (std::is_same<LY, LayF32>::value && ctx->p.nx % 4 == 0 && ctx->tile == 7) ? 1 : 0;
     kern<<<(unsigned)grid, step_block(ctx, TX * TY), smem, ctx->stream>>>(ctx->dp, zchunks, ly, ctx->type,
-                                                                        ctx->gray, ctx->macro, pf);
+                                                                        ctx->gray, ctx->macro);
     prof_end(ctx, "k_fused", e0);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;  // nothing ran: the state stays in buffer cur
@@ -71,14 +68,14 @@ static cudaError_t launch_fused_t(lbm_ctx *ctx, LY ly)
 
 // Geometries with reservoir cells, or a mass-sink-source rate, run the
 // instantiation that handles them; the others keep the plain march.
-template <int TX, int TY, int MINB, class LY>
+template <int TX, int TY, int MINB, class LY, bool PF = false, bool ML = false>
 static cudaError_t launch_fused_tile(lbm_ctx *ctx, bool write_macro, LY ly)
 {
     if (ctx->n_held > 0 || ctx->mss != 0.0)
-        return write_macro ? launch_fused_t<TX, TY, MINB, true, true>(ctx, ly)
-                           : launch_fused_t<TX, TY, MINB, false, true>(ctx, ly);
-    return write_macro ? launch_fused_t<TX, TY, MINB, true, false>(ctx, ly)
-                       : launch_fused_t<TX, TY, MINB, false, false>(ctx, ly);
+        return write_macro ? launch_fused_t<TX, TY, MINB, true, true, LY, PF, ML>(ctx, ly)
+                           : launch_fused_t<TX, TY, MINB, false, true, LY, PF, ML>(ctx, ly);
+    return write_macro ? launch_fused_t<TX, TY, MINB, true, false, LY, PF, ML>(ctx, ly)
+                       : launch_fused_t<TX, TY, MINB, false, false, LY, PF, ML>(ctx, ly);
 }
 
 // Tile variants: 0 = 32x8 (one CTA per SM, no register cap), 1 = 32x16
@@ -102,7 +99,9 @@ cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro)
     case 2: return launch_fused_tile<32, 8, 2>(ctx, write_macro, ly);
     case 3: return launch_fused_tile<32, 12, 1>(ctx, write_macro, ly);
     case 4: return launch_fused_tile<64, 8, 1>(ctx, write_macro, ly);
-    case 7: return launch_fused_tile<32, 8, 2>(ctx, write_macro, ly);
+    case 7: return launch_fused_tile<32, 8, 2, LayF32, true>(ctx, write_macro, ly);
+    case 8: return launch_fused_tile<32, 8, 2, LayF32, false, true>(ctx, write_macro, ly);
+    case 9: return launch_fused_tile<32, 8, 2, LayF32, true, true>(ctx, write_macro, ly);
     default: return launch_fused_tile<32, 8, 1>(ctx, write_macro, ly);
     }
 }

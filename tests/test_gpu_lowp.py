@@ -20,11 +20,15 @@ import lbm_cases as LC
 pytestmark = pytest.mark.gpu
 STORAGES = {"f32": 0, "f16": 1, "bf16": 2, "f16r": 3, "bf16r": 4}
 # Error bounds per storage, about 3x the errors measured on a GB300 (F32 is the
-# parity-level control).  The global shift cannot represent the momentum of
-# these slow flows (the velocity part of a population, ~1e-6, is below the
-# 16-bit resolution of f - w rho0, ~1e-5), so its permeability is bounded
-# only by an order of magnitude.
-BOUND_K = {"f32": 5e-4, "f16": 20.0, "bf16": 20.0, "f16r": 1e-3, "bf16r": 1e-2}
+# parity-level control).  The bundle is driven at g = 1e-3: along z it flows
+# 250x slower than along x, and at g = 1e-5 rounding-sized density changes
+# alone move K_z by 7e-6 in the FP64 oracle (test_oracle_conditioning), which
+# no FP32 path can undercut; at g = 1e-3 (Darcy flow, Re < 1e-3) by 7e-8.
+# The global shift cannot represent the momentum of these slow flows (the
+# velocity part of a population is near the 16-bit resolution of
+# f - w rho0, ~1e-5), so its permeability is bounded only loosely.
+FIBER_G = 1e-3
+BOUND_K = {"f32": 1e-5, "f16": 20.0, "bf16": 20.0, "f16r": 1e-3, "bf16r": 1e-2}
 BOUND_DP = {"f32": 1e-5, "f16": 0.1, "bf16": 0.05, "f16r": 5e-4, "bf16r": 2e-3}
 BOUND_SAT = {"f32": 1e-7, "f16": 2e-3, "bf16": 5e-3, "f16r": 1e-5, "bf16r": 1e-4}
 BOUND_MASS = {"f32": 1e-7, "f16": 0.1, "bf16": 0.2, "f16r": 5e-5, "bf16r": 5e-5}
@@ -37,6 +41,11 @@ def _oracle(name, steps, *args):
     return LC.run_oracle(case, steps)
 
 
+@functools.lru_cache(maxsize=None)
+def _oracle_fiber(steps, axis):
+    return LC.run_oracle(LC.fiber_flow(24, axis, g=FIBER_G), steps)
+
+
 def _rel(a, b):
     return abs(a - b) / abs(b)
 
@@ -44,11 +53,11 @@ def _rel(a, b):
 @pytest.mark.parametrize("storage", list(STORAGES))
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_permeability_fibre_bundle(storage, axis):
-    case = LC.fiber_flow(24, axis)
+    case = LC.fiber_flow(24, axis, g=FIBER_G)
     nu = (case.s["tau"][1] - 0.5) / 3.0
     g = case.s["accel"][1][axis]
     _, gobs, _ = LC.run_gpu(case, FIBER_STEPS, storage=STORAGES[storage])
-    _, oobs, _ = _oracle("fiber_flow", FIBER_STEPS, 24, axis)
+    _, oobs, _ = _oracle_fiber(FIBER_STEPS, axis)
     kg, ko = gobs["flux_vol"][axis] * nu / g, oobs["flux_vol"][axis] * nu / g
     err = _rel(kg, ko)
     print(f"permeability {storage} axis {'xyz'[axis]}: K_gpu {kg:.6e} K_oracle {ko:.6e} rel.err {err:.3e}")
