@@ -287,6 +287,9 @@ def run_ours(args, rank, world, local_rank):
     clocks.stop()
     ctx.close()
 
+    if obs["nan_count"] or obs_e2e["nan_count"]:
+        # a step whose fields went non-finite has no throughput to report
+        raise SystemExit(f"bench: non-finite fields after the timed steps ({obs['nan_count']} cells)")
     if rank != 0:
         if dist:
             dist.destroy_process_group()

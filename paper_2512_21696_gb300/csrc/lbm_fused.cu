@@ -11,7 +11,7 @@
 
 namespace lbm {
 
-template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY, bool PF = false, bool ML = false>
+template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY>
 __global__ void __launch_bounds__(TX *TY, MINB)
     k_fused(DevParams P, int zchunks, LY ly, const uint8_t *__restrict__ type, GrayRec *__restrict__ gray,
             float *__restrict__ macro)
@@ -25,16 +25,16 @@ __global__ void __launch_bounds__(TX *TY, MINB)
         const int za = (int)((long long)P.nz * chunk / zchunks);
         const int zb = (int)((long long)P.nz * (chunk + 1) / zchunks);
         if (za >= zb) continue;
-        fused_item<TX, TY, MACRO, EXT, LY, PF, ML>(P, G, ly, type, gray, macro, (col % tiles_x) * TX,
-                                                    (col / tiles_x) * TY, za, zb, smem_raw);
+        fused_item<TX, TY, MACRO, EXT>(P, G, ly, type, gray, macro, (col % tiles_x) * TX, (col / tiles_x) * TY, za,
+                                        zb, smem_raw);
     }
 }
 
 // ---------------------------------------------------------------------------
-template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY, bool PF = false, bool ML = false>
+template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY>
 static cudaError_t launch_fused_t(lbm_ctx *ctx, LY ly)
 {
-    auto kern = k_fused<TX, TY, MINB, MACRO, EXT, LY, PF, ML>;
+    auto kern = k_fused<TX, TY, MINB, MACRO, EXT, LY>;
     const size_t smem = Tiles<TX, TY>::smem();
     // launch configuration, resolved once per device
     static int cached_slots[64] = {};  // resident CTAs per device
@@ -68,14 +68,14 @@ static cudaError_t launch_fused_t(lbm_ctx *ctx, LY ly)
 
 // Geometries with reservoir cells, or a mass-sink-source rate, run the
 // instantiation that handles them; the others keep the plain march.
-template <int TX, int TY, int MINB, class LY, bool PF = false, bool ML = false>
+template <int TX, int TY, int MINB, class LY>
 static cudaError_t launch_fused_tile(lbm_ctx *ctx, bool write_macro, LY ly)
 {
     if (ctx->n_held > 0 || ctx->mss != 0.0)
-        return write_macro ? launch_fused_t<TX, TY, MINB, true, true, LY, PF, ML>(ctx, ly)
-                           : launch_fused_t<TX, TY, MINB, false, true, LY, PF, ML>(ctx, ly);
-    return write_macro ? launch_fused_t<TX, TY, MINB, true, false, LY, PF, ML>(ctx, ly)
-                       : launch_fused_t<TX, TY, MINB, false, false, LY, PF, ML>(ctx, ly);
+        return write_macro ? launch_fused_t<TX, TY, MINB, true, true>(ctx, ly)
+                           : launch_fused_t<TX, TY, MINB, false, true>(ctx, ly);
+    return write_macro ? launch_fused_t<TX, TY, MINB, true, false>(ctx, ly)
+                       : launch_fused_t<TX, TY, MINB, false, false>(ctx, ly);
 }
 
 // Tile variants: 0 = 32x8 (one CTA per SM, no register cap), 1 = 32x16
@@ -99,9 +99,7 @@ cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro)
     case 2: return launch_fused_tile<32, 8, 2>(ctx, write_macro, ly);
     case 3: return launch_fused_tile<32, 12, 1>(ctx, write_macro, ly);
     case 4: return launch_fused_tile<64, 8, 1>(ctx, write_macro, ly);
-    case 7: return launch_fused_tile<32, 8, 2, LayF32, true>(ctx, write_macro, ly);
-    case 8: return launch_fused_tile<32, 8, 2, LayF32, false, true>(ctx, write_macro, ly);
-    case 9: return launch_fused_tile<32, 8, 2, LayF32, true, true>(ctx, write_macro, ly);
+
     default: return launch_fused_tile<32, 8, 1>(ctx, write_macro, ly);
     }
 }

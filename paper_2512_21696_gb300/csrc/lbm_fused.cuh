@@ -58,13 +58,9 @@ __device__ __forceinline__ int ring3(int p) { return ((p % 3) + 3) % 3; }
 // One work item: the TX x TY columns at (x0, y0) over planes [za, zb) of the
 // lattice of shape G (G.n is the slot stride of ly, type, gray and macro),
 // physics P.  EXT compiles in the reservoir (inlet / outlet) cells and the
-// mass-sink-source term; without it neither is expected.  PF loads the raw
-// plane two ahead into registers before the collision and stores it after
-// (its memory latency then overlaps the collision instead of preceding a
-// barrier).  ML: a thread with two density-region cells loads both cells'
-// populations before summing either.  Ends with a block barrier, so the
-// rings can be reused at once.
-template <int TX, int TY, bool MACRO, bool EXT, class LY, bool PF = false, bool ML = false>
+// mass-sink-source term; without it neither is expected.  Ends with a block
+// barrier, so the rings can be reused at once.
+template <int TX, int TY, bool MACRO, bool EXT, class LY>
 __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, const LY &ly,
                                            const uint8_t *__restrict__ type,
                                            GrayRec *__restrict__ gray, float *__restrict__ macro, int x0, int y0,
@@ -101,122 +97,52 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
         RawCell *dst = raw + ring3(q) * T::RN;
         for (int e = tid; e < T::RN; e += T::NT) dst[e] = raw_entry(q, e);
     };
-    constexpr int RPT = (T::RN + T::NT - 1) / T::NT;  // raw entries per thread
 
     // ---- phase 1: drho of the den region (tile + 1-cell halo) at plane L ----
-    // One den-region cell e whose arrived populations (if fluid) are in gv.
-    auto den_finish = [&](int L, int e, const RawCell &me, int g, const float (&gv)[2][Q - 1]) {
+    auto densities = [&](int L) {
         const RawCell *r0 = raw + ring3(L - 1) * T::RN;
         const RawCell *r1 = raw + ring3(L) * T::RN;
         const RawCell *r2 = raw + ring3(L + 1) * T::RN;
-        const int dx = e % T::DX, dy = e / T::DX;
-        DenCell dc = {me.f0A, me.f0B, 0.f, 0.f, 0.f, 0.f};
-        if (me.type != CELL_SOLID) {
-            const bool held = EXT && is_held(me.type);
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                const int f0 = a ? me.f0B : me.f0A;
-                float acc = 0.f;
-                long long id = 0;
-#pragma unroll
-                for (int i = 1; i < Q; ++i) {
-                    const int o = opp(i);  // the source x - c_i is x + c_o
-                    const RawCell *rp = cz(o) < 0 ? r0 : (cz(o) > 0 ? r2 : r1);
-                    const RawCell &src = rp[(dx + 1 + cx(o)) + T::RX * (dy + 1 + cy(o))];
-                    acc += gv[a][i - 1];
-                    if (src.type != CELL_SOLID) id += (long long)((a ? src.f0B : src.f0A) - f0) * w12(i);
-                }
-                ff v = density_dev(id, acc);
-                if (held) v = held_dev(held_rho(G.held, me.type, a), f0);  // a reservoir's density is the held one
-                if (a) {
-                    dc.drB = v.hi;
-                    dc.loB = v.lo;
-                } else {
-                    dc.drA = v.hi;
-                    dc.loA = v.lo;
-                }
-            }
-        }
-        den[ring3(L) * T::DN + e] = dc;
-        dmeta[ring3(L) * T::DN + e] = {me.type, g};
-        dat[ring3(L) * T::DN + e] = me.type != CELL_SOLID ? atwood_of(P.wet, dc.f0A, dc.f0B, dc.drA, dc.drB) : P.at_wall;
-    };
-    // the raw entry and global index of den-region cell e (-1: solid or outside)
-    auto den_src = [&](int L, int e, RawCell &me) -> int {
-        const int dx = e % T::DX, dy = e / T::DX;
-        me = raw[ring3(L) * T::RN + (dx + 1) + T::RX * (dy + 1)];
-        if (me.type == CELL_SOLID) return -1;
+        DenCell *dd = den + ring3(L) * T::DN;
+        DenMeta *dm = dmeta + ring3(L) * T::DN;
+        float *da = dat + ring3(L) * T::DN;
         const int gz = wrap_coord(L, G.nz, P.per[2]);
-        return wrap_coord(x0 - 1 + dx, G.nx, P.per[0]) + G.nx * (wrap_coord(y0 - 1 + dy, G.ny, P.per[1]) + G.ny * gz);
-    };
-    auto densities = [&](int L) {
-        if constexpr (!ML) {
-            const RawCell *r0 = raw + ring3(L - 1) * T::RN;
-            const RawCell *r1 = raw + ring3(L) * T::RN;
-            const RawCell *r2 = raw + ring3(L + 1) * T::RN;
-            DenCell *dd = den + ring3(L) * T::DN;
-            DenMeta *dm = dmeta + ring3(L) * T::DN;
-            float *da = dat + ring3(L) * T::DN;
-            const int gz = wrap_coord(L, G.nz, P.per[2]);
-            for (int e = tid; e < T::DN; e += T::NT) {
-                const int dx = e % T::DX, dy = e / T::DX;
-                const RawCell me = r1[(dx + 1) + T::RX * (dy + 1)];
-                DenCell dc = {me.f0A, me.f0B, 0.f, 0.f, 0.f, 0.f};
-                int g = -1;
-                if (me.type != CELL_SOLID) {
-                    g = wrap_coord(x0 - 1 + dx, G.nx, P.per[0]) +
-                        G.nx * (wrap_coord(y0 - 1 + dy, G.ny, P.per[1]) + G.ny * gz);
-                    const bool held = EXT && is_held(me.type);
+        for (int e = tid; e < T::DN; e += T::NT) {
+            const int dx = e % T::DX, dy = e / T::DX;
+            const RawCell me = r1[(dx + 1) + T::RX * (dy + 1)];
+            DenCell dc = {me.f0A, me.f0B, 0.f, 0.f, 0.f, 0.f};
+            int g = -1;
+            if (me.type != CELL_SOLID) {
+                g = wrap_coord(x0 - 1 + dx, G.nx, P.per[0]) +
+                    G.nx * (wrap_coord(y0 - 1 + dy, G.ny, P.per[1]) + G.ny * gz);
+                const bool held = EXT && is_held(me.type);
 #pragma unroll
-                    for (int a = 0; a < 2; ++a) {
-                        const int f0 = a ? me.f0B : me.f0A;
-                        float acc = 0.f;
-                        long long id = 0;
+                for (int a = 0; a < 2; ++a) {
+                    const int f0 = a ? me.f0B : me.f0A;
+                    float acc = 0.f;
+                    long long id = 0;
 #pragma unroll
-                        for (int i = 1; i < Q; ++i) {
-                            const int o = opp(i);  // the source x - c_i is x + c_o
-                            const RawCell *rp = cz(o) < 0 ? r0 : (cz(o) > 0 ? r2 : r1);
-                            const RawCell &src = rp[(dx + 1 + cx(o)) + T::RX * (dy + 1 + cy(o))];
-                            acc += ly.mov_in(a, i, g);
-                            if (src.type != CELL_SOLID) id += (long long)((a ? src.f0B : src.f0A) - f0) * w12(i);
-                        }
-                        ff v = density_dev(id, acc);
-                        if (held) v = held_dev(held_rho(G.held, me.type, a), f0);  // a reservoir's density is the held one
-                        if (a) {
-                            dc.drB = v.hi;
-                            dc.loB = v.lo;
-                        } else {
-                            dc.drA = v.hi;
-                            dc.loA = v.lo;
-                        }
+                    for (int i = 1; i < Q; ++i) {
+                        const int o = opp(i);  // the source x - c_i is x + c_o
+                        const RawCell *rp = cz(o) < 0 ? r0 : (cz(o) > 0 ? r2 : r1);
+                        const RawCell &src = rp[(dx + 1 + cx(o)) + T::RX * (dy + 1 + cy(o))];
+                        acc += ly.mov_in(a, i, g);
+                        if (src.type != CELL_SOLID) id += (long long)((a ? src.f0B : src.f0A) - f0) * w12(i);
+                    }
+                    ff v = density_dev(id, acc);
+                    if (held) v = held_dev(held_rho(G.held, me.type, a), f0);  // a reservoir's density is the held one
+                    if (a) {
+                        dc.drB = v.hi;
+                        dc.loB = v.lo;
+                    } else {
+                        dc.drA = v.hi;
+                        dc.loA = v.lo;
                     }
                 }
-                dd[e] = dc;
-                dm[e] = {me.type, g};
-                da[e] = me.type != CELL_SOLID ? atwood_of(P.wet, dc.f0A, dc.f0B, dc.drA, dc.drB) : P.at_wall;
             }
-        } else {
-            // the cells tid and tid + NT: both cells' populations in flight at once
-            static_assert(T::DN <= 2 * T::NT, "at most two den-region cells per thread");
-            RawCell m0, m1;
-            const int e1 = tid + T::NT;
-            const int g0 = den_src(L, tid, m0);
-            const int g1 = e1 < T::DN ? den_src(L, e1, m1) : -1;
-            float v0[2][Q - 1], v1[2][Q - 1];
-            if (g0 >= 0) {
-#pragma unroll
-                for (int a = 0; a < 2; ++a)
-#pragma unroll
-                    for (int i = 1; i < Q; ++i) v0[a][i - 1] = ly.mov_in(a, i, g0);
-            }
-            if (g1 >= 0) {
-#pragma unroll
-                for (int a = 0; a < 2; ++a)
-#pragma unroll
-                    for (int i = 1; i < Q; ++i) v1[a][i - 1] = ly.mov_in(a, i, g1);
-            }
-            den_finish(L, tid, m0, g0, v0);
-            if (e1 < T::DN) den_finish(L, e1, m1, g1, v1);
+            dd[e] = dc;
+            dm[e] = {me.type, g};
+            da[e] = me.type != CELL_SOLID ? atwood_of(P.wet, dc.f0A, dc.f0B, dc.drA, dc.drB) : P.at_wall;
         }
     };
 
@@ -314,39 +240,14 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
                              tgt);
     };
 
-    if constexpr (!PF) {
-        load_raw(za - 2);
-        load_raw(za - 1);
-        for (int L = za - 1; L <= zb; ++L) {
-            load_raw(L + 1);
-            __syncthreads();
-            densities(L);
-            __syncthreads();
-            if (L - 1 >= za) collide(L - 1);
-        }
-    } else {
-        load_raw(za - 2);
-        load_raw(za - 1);
-        load_raw(za);
-        for (int L = za - 1; L <= zb; ++L) {
-            __syncthreads();  // raw planes L-1 .. L+1 in place
-            densities(L);
-            __syncthreads();
-            // raw plane L+2 into the slot of plane L-1, which densities(L) was the last to read
-            RawCell rv[RPT];
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const int e = tid + k * T::NT;
-                if (e < T::RN) rv[k] = raw_entry(L + 2, e);
-            }
-            if (L - 1 >= za) collide(L - 1);
-            RawCell *dst = raw + ring3(L + 2) * T::RN;
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const int e = tid + k * T::NT;
-                if (e < T::RN) dst[e] = rv[k];
-            }
-        }
+    load_raw(za - 2);
+    load_raw(za - 1);
+    for (int L = za - 1; L <= zb; ++L) {
+        load_raw(L + 1);
+        __syncthreads();
+        densities(L);
+        __syncthreads();
+        if (L - 1 >= za) collide(L - 1);
     }
     __syncthreads();
 }

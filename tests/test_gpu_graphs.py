@@ -59,6 +59,7 @@ def _same(case, calls, between=None, **kw):
     fa, sa, la = _run(case, calls, False, between, **kw)
     fb, sb, lb = _run(case, calls, True, between, **kw)
     for x, y in zip(fa, fb):
+        assert np.all(np.isfinite(x))  # equal arrays of NaN would compare equal
         np.testing.assert_array_equal(x, y)
     assert sa == sb
     assert la == lb  # every replayed launch is counted
@@ -158,6 +159,7 @@ def test_lbm_step_inside_a_callers_graph_capture():
         torch.cuda.synchronize()
         got = L.lbm_get_fields(ctx)
         for x, y in zip(want, got):
+            assert np.all(np.isfinite(x))
             np.testing.assert_array_equal(x, y)
     finally:
         ctx.close()

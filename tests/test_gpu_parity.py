@@ -273,6 +273,7 @@ def test_fused_matches_two_launch_path(tile):
     a, _, _ = LC.run_gpu(case, 25, path=0, tile=tile)
     b, _, _ = LC.run_gpu(case, 25, path=1)
     for x, y in zip(a, b):
+        assert np.all(np.isfinite(x)) and np.all(np.isfinite(y))
         np.testing.assert_allclose(x, y, rtol=0, atol=2e-6 * max(1.0, np.abs(y).max()))
 
 
@@ -336,7 +337,7 @@ def test_async_observables_equal_the_synchronous_ones():
         ctx.close()
 
 
-@pytest.mark.parametrize("tile", [5, 6, 7, 8, 9])
+@pytest.mark.parametrize("tile", [5, 6])
 @pytest.mark.parametrize("shape,periodic,steps", [((48, 48, 48), (1, 1, 1), 25), ((40, 37, 70), (1, 0, 1), 12),
                                                   ((9, 6, 11), (0, 1, 0), 12), ((128, 128, 128), (1, 1, 1), 3)])
 def test_march_is_bit_identical_to_rolling_window(shape, periodic, steps, tile):
@@ -350,7 +351,9 @@ def test_march_is_bit_identical_to_rolling_window(shape, periodic, steps, tile):
         case = LC.mixed_features(shape=shape, periodic=periodic, seed=sum(shape))
     a, ga, _ = LC.run_gpu(case, steps, path=0, tile=tile)
     b, gb, _ = LC.run_gpu(case, steps, path=0, tile=2)
+    assert ga["nan_count"] == 0 and gb["nan_count"] == 0  # equal arrays of NaN would compare equal
     for x, y in zip(a, b):
+        assert np.all(np.isfinite(y))
         np.testing.assert_array_equal(x, y)
     assert ga == gb
 
