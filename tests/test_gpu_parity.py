@@ -4,7 +4,12 @@ Tolerance: relative 1e-5 in the L2 norm over non-solid cells for rho^A,
 rho^B, u and Sw (FP32 kernels against the FP64 oracle on identical FP32
 inputs), and an element-wise bound max|x - x_or| / max|x_or| over the same
 cells (TOL_MAX), which a wrong value in one cell of a large lattice cannot
-pass.  Geometry results of the FP64 precompute are compared at FP32
+pass.  TOL_MAX is per quantity: the densities and Sw are O(1) and carry a few
+FP32 roundings per step (worst measured on a GB300 over every case here,
+including 400 steps at 128^3: 5.2e-7); u is a small difference of O(1)
+populations, so its error relative to max|u| is larger (worst measured 1.3e-5,
+in the droplet, where max|u| is the ~1e-4 spurious current).  Each bound is
+about 4x the worst measurement.  Geometry results of the FP64 precompute are compared at FP32
 rounding (2e-6 relative).
 """
 import numpy as np
@@ -16,7 +21,7 @@ from paper_2512_21696_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
-TOL_MAX = 1e-4
+TOL_MAX = {"rhoA": 2e-6, "rhoB": 2e-6, "u": 5e-5, "sw": 2e-6}
 
 
 def _compare(case, gpu, orc, tol=TOL, what=("rhoA", "rhoB", "u", "sw"), tol_max=TOL_MAX):
@@ -27,7 +32,7 @@ def _compare(case, gpu, orc, tol=TOL, what=("rhoA", "rhoB", "u", "sw"), tol_max=
     print(f"parity {case.name}: L2 {errs} max {emax}")
     for k in what:
         assert errs[k] <= tol, f"{case.name}: {k} relative L2 error {errs[k]:.3e} > {tol:.0e} ({errs})"
-        assert emax[k] <= tol_max, f"{case.name}: {k} element-wise error {emax[k]:.3e} > {tol_max:.0e} ({emax})"
+        assert emax[k] <= tol_max[k], f"{case.name}: {k} element-wise error {emax[k]:.3e} > {tol_max[k]:.0e} ({emax})"
     return errs
 
 
