@@ -94,6 +94,14 @@ __device__ __forceinline__ float cSc(int i, const float S[6])
            2.f * (cx(i) * cy(i) * S[3] + cx(i) * cz(i) * S[4] + cy(i) * cz(i) * S[5]);
 }
 
+// v[k] += x for a runtime index k of a two-element array, as selects (an
+// indexed access would put the array in local memory)
+__device__ __forceinline__ void add_at(float (&v)[2], int k, float x)
+{
+    v[0] += k == 0 ? x : 0.f;
+    v[1] += k == 1 ? x : 0.f;
+}
+
 __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *__restrict__ fin,
                                                   const float *__restrict__ rhob, const uint8_t *__restrict__ type,
                                                   const float *__restrict__ phi, const GrayRec *__restrict__ gray,
@@ -120,12 +128,15 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
     // ---------------- forward recomputation (FP32, plain populations) -------
     float f[2][Q];
     float rho[2], j[2][3], Pm[2][6];
+#pragma unroll
     for (int a = 0; a < 2; ++a) {
         const int f0 = fi[(size_t)a * Q * n + c];
         f[a][0] = (float)f0 * FIX_INV;
         rho[a] = f[a][0];
         j[a][0] = j[a][1] = j[a][2] = 0.f;
+#pragma unroll
         for (int k = 0; k < 6; ++k) Pm[a][k] = 0.f;
+#pragma unroll
         for (int i = 1; i < Q; ++i) {
             const int o = opp(i);
             const int fs = (wall & (1u << o)) ? f0 : fi[(size_t)a * Q * n + nb[o]];
@@ -145,6 +156,7 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
     }
     // neighbour densities seen by the stencils and their Atwood numbers
     float rn[2][Q], at[Q];
+#pragma unroll
     for (int i = 1; i < Q; ++i) {
         if (wall & (1u << i)) {
             rn[0][i] = P.rho_wall[0];
@@ -159,9 +171,13 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
     }
     const float rt = rho[0] + rho[1];
     float grad[2][3];
+#pragma unroll
     for (int b = 0; b < 2; ++b)
+#pragma unroll
         for (int d = 0; d < 3; ++d) grad[b][d] = 0.f;
+#pragma unroll
     for (int i = 1; i < Q; ++i)
+#pragma unroll
         for (int b = 0; b < 2; ++b) {
             grad[b][0] += w3(i) * cx(i) * rn[b][i];
             grad[b][1] += w3(i) * cy(i) * rn[b][i];
@@ -171,12 +187,15 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
     const bool csf = P.kappa != 0.0f && (P.csf_everywhere || is_gray);
     float Fp[2][3];  // forces before the drag
     float Hs[2][6], trH[2], sN[2], gHg[2], dv[2];  // CSF intermediates per component (a: H of rho^{1-a})
+#pragma unroll
     for (int a = 0; a < 2; ++a) {
         const float *g = grad[1 - a];
+#pragma unroll
         for (int d = 0; d < 3; ++d) Fp[a][d] = -P.G * rho[a] * g[d] + rho[a] * P.accel[a][d];
         if (csf) {
             const int b = 1 - a;
             float M6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, Lw = 0.f;
+#pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const float wd = wgt(i) * (rn[b][i] - rho[b]);
                 Lw += wd;
@@ -187,7 +206,9 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
                 M6[4] += cx(i) * cz(i) * wd;
                 M6[5] += cy(i) * cz(i) * wd;
             }
+#pragma unroll
             for (int k = 0; k < 3; ++k) Hs[a][k] = 9.f * M6[k] - 3.f * Lw;
+#pragma unroll
             for (int k = 3; k < 6; ++k) Hs[a][k] = 9.f * M6[k];
             trH[a] = Hs[a][0] + Hs[a][1] + Hs[a][2];
             float Hg[3];
@@ -196,11 +217,13 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
             sN[a] = sqrtf(dotn<3>(g, g) + P.eps_n * P.eps_n);
             dv[a] = trH[a] / sN[a] - gHg[a] / (sN[a] * sN[a] * sN[a]);
             const float kc = P.kappa * (-dv[a]) * P.csf_coef[a] * rho[a];
+#pragma unroll
             for (int d = 0; d < 3; ++d) Fp[a][d] += kc * g[d];
         }
     }
     const int w = P.wet;
-    const float rw = rho[w], rn_ = rho[1 - w];
+    const float nu_w = w ? P.nu[1] : P.nu[0], nu_n = w ? P.nu[0] : P.nu[1];
+    const float rw = w ? rho[1] : rho[0], rn_ = w ? rho[0] : rho[1];
     const float s_raw = (rw / rt - P.r_lo) * P.inv_r_span;
     const float s = fminf(fmaxf(s_raw, 0.f), 1.f);
     float sw = s, Rw = 0.f, Ro = 0.f;
@@ -224,6 +247,7 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
         Ro = (swd && wetf) ? gr.b.z : 0.f;
         sw = Rw + (1.f - Rw - Ro) * s;
         cv = P.curve[meta & 0xffu];
+#pragma unroll
         for (int i = 1; i < Q; ++i) {
             gAt[0] += w3(i) * cx(i) * at[i];
             gAt[1] += w3(i) * cy(i) * at[i];
@@ -238,39 +262,49 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
             Pc = pcs * pc_shape(cv, se_c, pw_unused);
             mden = fmaxf(mag, P.eps_n);
             kcap = -Pc * Hh / (mden * rt);
+#pragma unroll
             for (int a = 0; a < 2; ++a)
+#pragma unroll
                 for (int d = 0; d < 3; ++d) Fp[a][d] += kcap * rho[a] * gAt[d];
         }
         se_k = fminf(fmaxf((sw - cv.swr) * cv.inv_1m_swr, 0.f), 1.f);
         krw = powf(se_k, cv.nw);
         krn = powf(1.f - se_k, cv.nn);
-        coef = rw * P.nu[w] / fmaxf(krw, P.kr_min) + rn_ * P.nu[1 - w] / fmaxf(krn, P.kr_min);
+        coef = rw * nu_w / fmaxf(krw, P.kr_min) + rn_ * nu_n / fmaxf(krn, P.kr_min);
         rk = coef * iK0;
     }
     float bb[3], u[3];
+#pragma unroll
     for (int d = 0; d < 3; ++d) bb[d] = j[0][d] + j[1][d] + 0.5f * (Fp[0][d] + Fp[1][d]);
     float al = 1.f, be = 0.f;
     if (is_gray) {
         al = rt + 0.5f * rk;
         be = 0.5f * rk;
         const float q = be * dotn<3>(gv, bb) / (al + be * dotn<3>(gv, gv));
+#pragma unroll
         for (int d = 0; d < 3; ++d) u[d] = (bb[d] - q * gv[d]) / al;
     } else {
+#pragma unroll
         for (int d = 0; d < 3; ++d) u[d] = bb[d] / rt;
     }
     float Ru[3] = {0.f, 0.f, 0.f}, F[2][3];
     const float vu = dotn<3>(gv, u);
     if (is_gray)
+#pragma unroll
         for (int d = 0; d < 3; ++d) Ru[d] = rk * (u[d] + gv[d] * vu);
+#pragma unroll
     for (int a = 0; a < 2; ++a)
+#pragma unroll
         for (int d = 0; d < 3; ++d) F[a][d] = Fp[a][d] - (is_gray ? (rho[a] / rt) * Ru[d] : 0.f);
 
     // ---------------- reverse ----------------------------------------------
     float lrho[2] = {0.f, 0.f}, lj[3] = {0.f, 0.f, 0.f}, lP[2][6], lF[2][3], lu[3] = {0.f, 0.f, 0.f};
     const float uu = dotn<3>(u, u);
+#pragma unroll
     for (int a = 0; a < 2; ++a) {
         // adjoints of the 19 outputs at their push targets
         float L0 = 0.f, L1[3] = {0.f, 0.f, 0.f}, L2[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
         for (int i = 0; i < Q; ++i) {
             size_t tg;
             if (i == 0) tg = c;
@@ -293,7 +327,9 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
         symv(L2, u, L2u);
         // lambda_Pi = 4.5 om (L2 - L0 I / 3)
         float lPi[6];
+#pragma unroll
         for (int k = 0; k < 6; ++k) lPi[k] = 4.5f * om * L2[k];
+#pragma unroll
         for (int k = 0; k < 3; ++k) lPi[k] -= 1.5f * om * L0;
         float lPiu[3], lPiF[3];
         symv(lPi, u, lPiu);
@@ -302,11 +338,13 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
         symv(L2, F[a], L2F);
         lrho[a] += L0 + 3.f * dotn<3>(u, L1) + 4.5f * dotn<3>(u, L2u) - 1.5f * uu * L0;
         lrho[a] += -(lPi[0] + lPi[1] + lPi[2]) * (1.0f / 3.0f) - dotn<3>(u, lPiu);
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
             lF[a][d] = 1.5f * L1[d] + 4.5f * L2u[d] - 1.5f * L0 * u[d] + lPiu[d];
             lu[d] += rho[a] * (3.f * L1[d] + 9.f * L2u[d] - 3.f * L0 * u[d]) + 4.5f * L2F[d] - 1.5f * L0 * F[a][d] -
                      2.f * rho[a] * lPiu[d] + lPiF[d];
         }
+#pragma unroll
         for (int k = 0; k < 6; ++k) lP[a][k] = lPi[k];
     }
     float lsw = 0.f;
@@ -318,7 +356,9 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
     // drag: F = Fp - (rho_a/rt) Ru, Ru = rk (u + v (v.u))
     if (is_gray) {
         float lRu[3];
+#pragma unroll
         for (int d = 0; d < 3; ++d) lRu[d] = -(rho[0] * lF[0][d] + rho[1] * lF[1][d]) / rt;
+#pragma unroll
         for (int a = 0; a < 2; ++a) {
             const float RuF = dotn<3>(Ru, lF[a]);
             lrho[a] += -RuF / rt;
@@ -326,37 +366,46 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
         }
         const float vlRu = dotn<3>(gv, lRu);
         float uvv[3];
+#pragma unroll
         for (int d = 0; d < 3; ++d) uvv[d] = u[d] + gv[d] * vu;
         lrk += dotn<3>(lRu, uvv);
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
             lu[d] += rk * (lRu[d] + gv[d] * vlRu);
             lv[d] += rk * (vu * lRu[d] + vlRu * u[d]);
         }
     }
+#pragma unroll
     for (int a = 0; a < 2; ++a)
+#pragma unroll
         for (int d = 0; d < 3; ++d) lFp[a][d] = lF[a][d];
     // velocity
     float lb[3];
     if (is_gray) {
         // (al I + be v v^T) u = b: lb = A^-1 lu, lA = -lb u^T
         const float q = be * dotn<3>(gv, lu) / (al + be * dotn<3>(gv, gv));
+#pragma unroll
         for (int d = 0; d < 3; ++d) lb[d] = (lu[d] - q * gv[d]) / al;
         const float lal = -dotn<3>(lb, u);
         const float vz = dotn<3>(gv, lb);
         const float lbe = -vz * vu;
+#pragma unroll
         for (int d = 0; d < 3; ++d) lv[d] += -be * (vu * lb[d] + vz * u[d]);
         lrt += lal;
         lrk += 0.5f * lal + 0.5f * lbe;
     } else {
+#pragma unroll
         for (int d = 0; d < 3; ++d) lb[d] = lu[d] / rt;
         lrt += -dotn<3>(u, lu) / rt;
     }
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
         lj[d] = lb[d];
         lFp[0][d] += 0.5f * lb[d];
         lFp[1][d] += 0.5f * lb[d];
     }
     float lrn[2][Q], lat[Q];
+#pragma unroll
     for (int i = 0; i < Q; ++i) {
         lrn[0][i] = lrn[1][i] = 0.f;
         lat[i] = 0.f;
@@ -367,10 +416,10 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
         const float lcoef = lrk * iK0;
         lgk[0] += lrk * coef;
         const float mw = fmaxf(krw, P.kr_min), mn = fmaxf(krn, P.kr_min);
-        lrho[w] += lcoef * P.nu[w] / mw;
-        lrho[1 - w] += lcoef * P.nu[1 - w] / mn;
-        const float lkrw = krw > P.kr_min ? -lcoef * rw * P.nu[w] / (mw * mw) : 0.f;
-        const float lkrn = krn > P.kr_min ? -lcoef * rn_ * P.nu[1 - w] / (mn * mn) : 0.f;
+        add_at(lrho, w, lcoef * nu_w / mw);
+        add_at(lrho, 1 - w, lcoef * nu_n / mn);
+        const float lkrw = krw > P.kr_min ? -lcoef * rw * nu_w / (mw * mw) : 0.f;
+        const float lkrn = krn > P.kr_min ? -lcoef * rn_ * nu_n / (mn * mn) : 0.f;
         float lsek = 0.f;
         if (se_k > 0.f) lsek += lkrw * cv.nw * powf(se_k, cv.nw - 1.f);
         if (se_k < 1.f) lsek += -lkrn * cv.nn * powf(1.f - se_k, cv.nn - 1.f);
@@ -379,10 +428,12 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
         // capillary: Fp += k rho_a gAt, k = -Pc Hh / (mden rt)
         if (Hh > 0.f) {
             float lk = 0.f, lgat[3] = {0.f, 0.f, 0.f};
+#pragma unroll
             for (int a = 0; a < 2; ++a) {
                 const float gl = dotn<3>(gAt, lFp[a]);
                 lk += rho[a] * gl;
                 lrho[a] += kcap * gl;
+#pragma unroll
                 for (int d = 0; d < 3; ++d) lgat[d] += kcap * rho[a] * lFp[a][d];
             }
             const float lPc = -lk * Hh / (mden * rt);
@@ -391,6 +442,7 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
             lrt += lk * Pc * Hh / (mden * rt * rt);
             const float lmag = 0.5f * lHh + (mag > P.eps_n ? lm : 0.f);
             if (mag > 0.f)
+#pragma unroll
                 for (int d = 0; d < 3; ++d) lgat[d] += lmag * gAt[d] / mag;
             // Pc = pcs pw(se_c)
             float dpw;
@@ -399,6 +451,7 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
             const float lsec = lPc * pcs * dpw;
             const float sec_raw = (sw - cv.swr) * cv.inv_1m_swr;
             if (sec_raw > 1e-2f && sec_raw < 1.f) lsw += lsec * cv.inv_1m_swr;
+#pragma unroll
             for (int i = 1; i < Q; ++i)
                 if (!(wall & (1u << i))) lat[i] = w3(i) * (cx(i) * lgat[0] + cy(i) * lgat[1] + cz(i) * lgat[2]);
         }
@@ -410,14 +463,16 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
     // s = clamp((rho_w/rt - r_lo) / span)
     if (s_raw > 0.f && s_raw < 1.f) {
         const float ls = lsw * P.inv_r_span;
-        lrho[w] += ls / rt;
+        add_at(lrho, w, ls / rt);
         lrt += -ls * rw / (rt * rt);
     }
     float lgrad[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
     for (int a = 0; a < 2; ++a) {
         const float *g = grad[1 - a];
         // body and Shan-Chen
         lrho[a] += dotn<3>(P.accel[a], lFp[a]) - P.G * dotn<3>(g, lFp[a]);
+#pragma unroll
         for (int d = 0; d < 3; ++d) lgrad[1 - a][d] += -P.G * rho[a] * lFp[a][d];
         if (csf) {
             const int b = 1 - a;
@@ -426,6 +481,7 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
             const float ldiv = -kc * rho[a] * gl;
             lrho[a] += kc * (-dv[a]) * gl;
             float lg[3];
+#pragma unroll
             for (int d = 0; d < 3; ++d) lg[d] = kc * (-dv[a]) * rho[a] * lFp[a][d];
             const float s3 = sN[a] * sN[a] * sN[a];
             const float ltr = ldiv / sN[a];
@@ -433,38 +489,47 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
             const float ls = ldiv * (-trH[a] / (sN[a] * sN[a]) + 3.f * gHg[a] / (s3 * sN[a]));
             float Hg[3];
             symv(Hs[a], g, Hg);
+#pragma unroll
             for (int d = 0; d < 3; ++d) lg[d] += 2.f * lgHg * Hg[d] + ls * g[d] / sN[a];
             // lambda_H = lgHg g g^T + ltr I  -> per direction q_i = w_i (9 c.lH.c - 3 tr lH)
             float lH[6] = {lgHg * g[0] * g[0] + ltr, lgHg * g[1] * g[1] + ltr, lgHg * g[2] * g[2] + ltr,
                            lgHg * g[0] * g[1], lgHg * g[0] * g[2], lgHg * g[1] * g[2]};
             const float trl = lH[0] + lH[1] + lH[2];
+#pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const float qi = wgt(i) * (9.f * cSc(i, lH) - 3.f * trl);
                 if (!(wall & (1u << i))) lrn[b][i] += qi;
                 lrho[b] -= qi;
             }
+#pragma unroll
             for (int d = 0; d < 3; ++d) lgrad[b][d] += lg[d];
         }
     }
     // grad[b] = sum_i 3 w_i c_i rn[b][i]
+#pragma unroll
     for (int i = 1; i < Q; ++i)
         if (!(wall & (1u << i)))
+#pragma unroll
             for (int b = 0; b < 2; ++b)
                 lrn[b][i] += w3(i) * (cx(i) * lgrad[b][0] + cy(i) * lgrad[b][1] + cz(i) * lgrad[b][2]);
     // Atwood numbers of the neighbours: At = (rw - rn)/(rw + rn)
     if (is_gray)
+#pragma unroll
         for (int i = 1; i < Q; ++i)
             if (!(wall & (1u << i)) && lat[i] != 0.f) {
-                const float a_w = rn[w][i], a_n = rn[1 - w][i], den = a_w + a_n;
+                const float a_w = w ? rn[1][i] : rn[0][i], a_n = w ? rn[0][i] : rn[1][i], den = a_w + a_n;
                 if (den > 0.f) {
-                    lrn[w][i] += lat[i] * 2.f * a_n / (den * den);
-                    lrn[1 - w][i] += -lat[i] * 2.f * a_w / (den * den);
+                    const float dw = lat[i] * 2.f * a_n / (den * den), dn = -lat[i] * 2.f * a_w / (den * den);
+                    lrn[0][i] += w ? dn : dw;
+                    lrn[1][i] += w ? dw : dn;
                 }
             }
     lrho[0] += lrt;
     lrho[1] += lrt;
     // own populations: rho_a = sum f, j = sum c f (both components), P_a = sum c c f
+#pragma unroll
     for (int a = 0; a < 2; ++a) {
+#pragma unroll
         for (int i = 0; i < Q; ++i) {
             const float v = lrho[a] + cx(i) * lj[0] + cy(i) * lj[1] + cz(i) * lj[2] + cSc(i, lP[a]);
             lam_out[(size_t)a * Q * n + (size_t)i * n + c] = v;
@@ -472,6 +537,7 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
     }
     // the adjoint of neighbour x + c_i's density, read back by that neighbour
     // (zero towards walls, which have no density)
+#pragma unroll
     for (int i = 1; i < Q; ++i) {
         const bool wl = wall & (1u << i);
         contrib[(size_t)i * n + c] = wl ? 0.f : lrn[0][i];
