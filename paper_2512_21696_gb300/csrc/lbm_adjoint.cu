@@ -816,11 +816,12 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
     cudaStream_t s = ctx->stream;
     // checkpoints (state + gray records at each segment start), one segment of
     // states (ckpt + 1) and gray snapshots (ckpt), adjoint buffers
-    DevBuf ck_f, ck_g, seg_f, seg_g, lam0, lam1, acc, gacc, dphi, fin_f, fin_g;
+    DevBuf ck_f, ck_g, seg_f, seg_g, seg_r, lam0, lam1, acc, gacc, dphi, fin_f, fin_g;
     LBM_CUDA(cudaMalloc(&ck_f.p, pb * nseg));
     LBM_CUDA(cudaMalloc(&ck_g.p, gb * nseg));
     LBM_CUDA(cudaMalloc(&seg_f.p, pb * (ckpt + 1)));
     LBM_CUDA(cudaMalloc(&seg_g.p, gb * ckpt));
+    LBM_CUDA(cudaMalloc(&seg_r.p, 3 * (size_t)n * sizeof(float) * ckpt));  // densities of each replayed state
     LBM_CUDA(cudaMalloc(&lam0.p, pb));
     LBM_CUDA(cudaMalloc(&lam1.p, pb));
     LBM_CUDA(cudaMalloc(&acc.p, 2 * Q * (size_t)n * sizeof(float)));  // contrib[2][Q][n]
@@ -829,12 +830,14 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
     LBM_CUDA(cudaMalloc(&fin_f.p, pb));
     LBM_CUDA(cudaMalloc(&fin_g.p, gb));
     char *ckf = (char *)ck_f.p, *ckg = (char *)ck_g.p, *sf = (char *)seg_f.p, *sg = (char *)seg_g.p;
+    float *const sr = (float *)seg_r.p;
     float *const f_save[2] = {ctx->f[0], ctx->f[1]};
     const int cur_save = ctx->cur;
     const long long steps0 = ctx->steps;
     auto restore_ptrs = [&]() {
         ctx->f[0] = f_save[0];
         ctx->f[1] = f_save[1];
+        ctx->rho_cap = nullptr;
     };
     // ---- forward with checkpoints ----
     for (int k = 0; k < nsteps; ++k) {
@@ -875,23 +878,25 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
         const int k0 = sgi * ckpt, k1 = std::min(nsteps, k0 + ckpt);
         cudaError_t e = cudaMemcpyAsync(sf, ckf + pb * sgi, pb, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->gray, ckg + gb * sgi, gb, cudaMemcpyDeviceToDevice, s);
-        // recompute the segment, keeping every state and the gray records each step used
+        // recompute the segment, keeping every state, the gray records each
+        // step used and the densities each step formed (the same values as
+        // the density pass of the two-launch path)
         for (int k = k0; k < k1 && e == cudaSuccess; ++k) {
             ctx->f[0] = (float *)(sf + pb * (k - k0));
             ctx->f[1] = (float *)(sf + pb * (k - k0 + 1));
             ctx->cur = 0;
+            ctx->rho_cap = sr + 3 * (size_t)n * (k - k0);
             e = launch_fused(ctx, false);
+            ctx->rho_cap = nullptr;
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(sg + gb * (k - k0), ctx->gray, gb, cudaMemcpyDeviceToDevice, s);
         }
         for (int k = k1 - 1; k >= k0 && e == cudaSuccess; --k) {
             ctx->f[0] = (float *)(sf + pb * (k - k0));
             ctx->cur = 0;
-            e = launch_density(ctx);
-            if (e != cudaSuccess) break;
             AdjSeed sk = seed;
             sk.on = (k == nsteps - 1);
-            k_adj_cell<<<grid, 128, 0, s>>>(ctx->dp, ctx->f[0], ctx->rho, ctx->type, ctx->phi,
+            k_adj_cell<<<grid, 128, 0, s>>>(ctx->dp, ctx->f[0], sr + 3 * (size_t)n * (k - k0), ctx->type, ctx->phi,
                                               (const GrayRec *)(sg + gb * (k - k0)), lam_next, lam_cur,
                                               (float *)acc.p, (double *)gacc.p, sk);
             k_adj_finish<<<grid, 128, 0, s>>>(ctx->dp, ctx->type, lam_cur, (const float *)acc.p);

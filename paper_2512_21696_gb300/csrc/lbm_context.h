@@ -30,6 +30,7 @@ struct lbm_ctx {
     float *phi = nullptr;              // [n] porosity (1 pore, 0 solid)
     lbm::GrayRec *gray = nullptr;      // [n], valid at gray cells only
     float *rho = nullptr;              // [2][n] densities of the current step
+    float *rho_cap = nullptr;          // [3][n]: while set, fused steps also store their densities there
     float *macro = nullptr;            // [6][n] rhoA, rhoB, ux, uy, uz, Sw
     double *red = nullptr;             // reduction partials
     int red_blocks = 0;

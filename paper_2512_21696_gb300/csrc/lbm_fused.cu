@@ -11,10 +11,10 @@
 
 namespace lbm {
 
-template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY>
+template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY, bool CAP = false>
 __global__ void __launch_bounds__(TX *TY, MINB)
     k_fused(DevParams P, int zchunks, LY ly, const uint8_t *__restrict__ type, GrayRec *__restrict__ gray,
-            float *__restrict__ macro)
+            float *__restrict__ macro, float *__restrict__ cap)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Geo G = geo_of(P);
@@ -25,16 +25,16 @@ __global__ void __launch_bounds__(TX *TY, MINB)
         const int za = (int)((long long)P.nz * chunk / zchunks);
         const int zb = (int)((long long)P.nz * (chunk + 1) / zchunks);
         if (za >= zb) continue;
-        fused_item<TX, TY, MACRO, EXT>(P, G, ly, type, gray, macro, (col % tiles_x) * TX, (col / tiles_x) * TY, za,
-                                        zb, smem_raw);
+        fused_item<TX, TY, MACRO, EXT, LY, CAP>(P, G, ly, type, gray, macro, (col % tiles_x) * TX,
+                                                (col / tiles_x) * TY, za, zb, smem_raw, cap);
     }
 }
 
 // ---------------------------------------------------------------------------
-template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY>
+template <int TX, int TY, int MINB, bool MACRO, bool EXT, class LY, bool CAP = false>
 static cudaError_t launch_fused_t(lbm_ctx *ctx, LY ly)
 {
-    auto kern = k_fused<TX, TY, MINB, MACRO, EXT, LY>;
+    auto kern = k_fused<TX, TY, MINB, MACRO, EXT, LY, CAP>;
     const size_t smem = Tiles<TX, TY>::smem();
     // launch configuration, resolved once per device
     static int cached_slots[64] = {};  // resident CTAs per device
@@ -57,7 +57,7 @@ static cudaError_t launch_fused_t(lbm_ctx *ctx, LY ly)
     cudaEvent_t e0;
     prof_begin(ctx, "k_fused", &e0);
     kern<<<(unsigned)grid, step_block(ctx, TX * TY), smem, ctx->stream>>>(ctx->dp, zchunks, ly, ctx->type,
-                                                                        ctx->gray, ctx->macro);
+                                                                        ctx->gray, ctx->macro, ctx->rho_cap);
     prof_end(ctx, "k_fused", e0);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;  // nothing ran: the state stays in buffer cur
@@ -84,6 +84,12 @@ static cudaError_t launch_fused_tile(lbm_ctx *ctx, bool write_macro, LY ly)
 // The rest-referenced 16-bit layouts run the default tile.
 cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro)
 {
+    if (ctx->rho_cap) {  // the adjoint's replay: plain F32 steps that also store their densities
+        if (ctx->p.storage != LBM_STORAGE_F32 || write_macro || ctx->n_held > 0 || ctx->mss != 0.0)
+            return cudaErrorInvalidValue;
+        return launch_fused_t<32, 8, 2, false, false, LayF32, true>(ctx, LayF32{ctx->f[ctx->cur], ctx->f[1 - ctx->cur],
+                                                                            ctx->n});
+    }
     if (ctx->tile == 5 || ctx->tile == 6) {  // the published-density march where it applies, else tile 2
         bool ran = false;
         const cudaError_t e = launch_march(ctx, write_macro, &ran);

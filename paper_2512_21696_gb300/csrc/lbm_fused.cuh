@@ -60,11 +60,14 @@ __device__ __forceinline__ int ring3(int p) { return ((p % 3) + 3) % 3; }
 // physics P.  EXT compiles in the reservoir (inlet / outlet) cells and the
 // mass-sink-source term; without it neither is expected.  Ends with a block
 // barrier, so the rings can be reused at once.
-template <int TX, int TY, bool MACRO, bool EXT, class LY>
+// CAP: the densities of the tile's own cells (rho - 3 f_0 of both
+// components and the Atwood number, the values the two-launch path's density
+// pass writes) are also stored into cap[3][n], for the adjoint's replay.
+template <int TX, int TY, bool MACRO, bool EXT, class LY, bool CAP = false>
 __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, const LY &ly,
                                            const uint8_t *__restrict__ type,
                                            GrayRec *__restrict__ gray, float *__restrict__ macro, int x0, int y0,
-                                           int za, int zb, unsigned char *smem_raw)
+                                           int za, int zb, unsigned char *smem_raw, float *__restrict__ cap = nullptr)
 {
     using T = Tiles<TX, TY>;
     RawCell *raw = reinterpret_cast<RawCell *>(smem_raw);         // [3][RN]
@@ -143,6 +146,12 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
             dd[e] = dc;
             dm[e] = {me.type, g};
             da[e] = me.type != CELL_SOLID ? atwood_of(P.wet, dc.f0A, dc.f0B, dc.drA, dc.drB) : P.at_wall;
+            if (CAP && g >= 0 && L >= za && L < zb && dx >= 1 && dx <= TX && dy >= 1 && dy <= TY &&
+                x0 - 1 + dx < G.nx && y0 - 1 + dy < G.ny) {
+                cap[g] = dc.drA;
+                cap[(size_t)n + g] = dc.drB;
+                cap[(size_t)2 * n + g] = da[e];
+            }
         }
     };
 
