@@ -5,7 +5,8 @@
 // One adjoint step (going backwards, step n):
 //   k_adj_cell   per fluid cell x: recomputes the cell's forward map in FP32
 //                from the stored state of step n, takes the adjoints of its 38
-//                outputs from lam^{n+1} at their push targets, and runs the
+//                outputs from lam^{n+1} at their push targets (own part plus
+//                the target cell's gathered neighbour term), and runs the
 //                map in reverse: moments, regularised collision with the
 //                Eq. 3 force term, semi-implicit velocity (Sherman-Morrison),
 //                drag, capillary term, residual saturation, CSF curvature,
@@ -14,10 +15,12 @@
 //                (one slot per direction, contrib[b][i][x]) and accumulates
 //                the adjoints of its gray constants (v = sqrt(a-1) e1, 1/K0,
 //                lamL*pd, Sw_irr, So_res);
-//   k_adj_finish lam^n(y) = own part + sum_i contrib[b][i][y - c_i] on every
-//                slot of y (rho = sum f): the adjoint of a push is a pull, so
-//                the neighbour terms are gathered in a fixed order (no
-//                atomics; the gradient does not depend on the scheduling).
+//   k_adj_finish V^n(y) = sum_i contrib[b][i][y - c_i], the neighbour term,
+//                the same on every slot of y (rho = sum f), so stored once
+//                per cell and component and added where lam^n is read: the
+//                adjoint of a push is a pull, so the neighbour terms are
+//                gathered in a fixed order (no atomics; the gradient does not
+//                depend on the scheduling).
 // After the last adjoint step k_geom_adjoint chains the gray constants to phi
 // (Kozeny-Carman, Leverett, the residual crossings and the principal axis,
 // d e1 = sum_{k != 1} e_k (e_k^T dM e1)/(mu1 - mu_k)), in FP64.
@@ -105,7 +108,8 @@ __device__ __forceinline__ void add_at(float (&v)[2], int k, float x)
 __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *__restrict__ fin,
                                                   const float *__restrict__ rhob, const uint8_t *__restrict__ type,
                                                   const float *__restrict__ phi, const GrayRec *__restrict__ gray,
-                                                  const float *__restrict__ lam_next, float *__restrict__ lam_out,
+                                                  const float *__restrict__ lam_next,
+                                                  const float *__restrict__ v_next, float *__restrict__ lam_out,
                                                   float *__restrict__ contrib, double *__restrict__ gacc,
                                                   AdjSeed seed)
 {
@@ -307,10 +311,14 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             size_t tg;
+            int tc = c;  // the target cell
             if (i == 0) tg = c;
             else if (wall & (1u << i)) tg = (size_t)opp(i) * n + c;
-            else tg = (size_t)i * n + nb[i];
-            const float li = wgt(i) * lam_next[(size_t)a * Q * n + tg];
+            else {
+                tc = nb[i];
+                tg = (size_t)i * n + tc;
+            }
+            const float li = wgt(i) * (lam_next[(size_t)a * Q * n + tg] + v_next[(size_t)a * n + tc]);
             L0 += li;
             L1[0] += cx(i) * li;
             L1[1] += cy(i) * li;
@@ -555,7 +563,7 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
     }
 }
 
-__global__ void k_adj_finish(DevParams P, const uint8_t *__restrict__ type, float *__restrict__ lam,
+__global__ void k_adj_finish(DevParams P, const uint8_t *__restrict__ type, float *__restrict__ vout,
                              const float *__restrict__ contrib)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -577,12 +585,8 @@ __global__ void k_adj_finish(DevParams P, const uint8_t *__restrict__ type, floa
             v[1] += contrib[(size_t)(Q + i) * n + s];
         }
     }
-    for (int a = 0; a < 2; ++a) {
-        for (int i = 0; i < Q; ++i) {
-            float &l = lam[(size_t)a * Q * n + (size_t)i * n + c];
-            l = solid ? 0.f : l + v[a];
-        }
-    }
+    vout[c] = v[0];
+    vout[(size_t)n + c] = v[1];
 }
 
 // d S / d phi_c = (Sw_c - S) / sum(phi) at gray cells (the weights of the
@@ -816,7 +820,7 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
     cudaStream_t s = ctx->stream;
     // checkpoints (state + gray records at each segment start), one segment of
     // states (ckpt + 1) and gray snapshots (ckpt), adjoint buffers
-    DevBuf ck_f, ck_g, seg_f, seg_g, seg_r, lam0, lam1, acc, gacc, dphi, fin_f, fin_g;
+    DevBuf ck_f, ck_g, seg_f, seg_g, seg_r, lam0, lam1, vb0, vb1, acc, gacc, dphi, fin_f, fin_g;
     LBM_CUDA(cudaMalloc(&ck_f.p, pb * nseg));
     LBM_CUDA(cudaMalloc(&ck_g.p, gb * nseg));
     LBM_CUDA(cudaMalloc(&seg_f.p, pb * (ckpt + 1)));
@@ -824,6 +828,8 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
     LBM_CUDA(cudaMalloc(&seg_r.p, 3 * (size_t)n * sizeof(float) * ckpt));  // densities of each replayed state
     LBM_CUDA(cudaMalloc(&lam0.p, pb));
     LBM_CUDA(cudaMalloc(&lam1.p, pb));
+    LBM_CUDA(cudaMalloc(&vb0.p, 2 * (size_t)n * sizeof(float)));  // neighbour terms V[2][n]
+    LBM_CUDA(cudaMalloc(&vb1.p, 2 * (size_t)n * sizeof(float)));
     LBM_CUDA(cudaMalloc(&acc.p, 2 * Q * (size_t)n * sizeof(float)));  // contrib[2][Q][n]
     LBM_CUDA(cudaMalloc(&gacc.p, 8 * (size_t)n * sizeof(double)));
     LBM_CUDA(cudaMalloc(&dphi.p, (size_t)n * sizeof(double)));
@@ -865,6 +871,9 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
     seed.lux = (float)(dLdq / ((double)ctx->p.ny * ctx->p.nz));
     seed.lsw = (float)(sumphi > 0 ? dLdS / sumphi : 0.0);
     LBM_CUDA(cudaMemsetAsync(lam0.p, 0, pb, s));
+    LBM_CUDA(cudaMemsetAsync(lam1.p, 0, pb, s));
+    LBM_CUDA(cudaMemsetAsync(vb0.p, 0, 2 * (size_t)n * sizeof(float), s));
+    LBM_CUDA(cudaMemsetAsync(vb1.p, 0, 2 * (size_t)n * sizeof(float), s));
     LBM_CUDA(cudaMemsetAsync(acc.p, 0, 2 * Q * (size_t)n * sizeof(float), s));
     LBM_CUDA(cudaMemsetAsync(gacc.p, 0, 8 * (size_t)n * sizeof(double), s));
     LBM_CUDA(cudaMemsetAsync(dphi.p, 0, (size_t)n * sizeof(double), s));
@@ -872,6 +881,7 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
     if (sumphi > 0)
         k_sat_weight_grad<<<grid, 128, 0, s>>>(n, ctx->type, ctx->macro, dLdS, S, sumphi, (double *)dphi.p);
     float *lam_next = (float *)lam0.p, *lam_cur = (float *)lam1.p;
+    float *v_next = (float *)vb0.p, *v_cur = (float *)vb1.p;
     // ---- backwards, segment by segment ----
     int rc = LBM_OK;
     for (int sgi = nseg - 1; sgi >= 0 && rc == LBM_OK; --sgi) {
@@ -897,12 +907,13 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
             AdjSeed sk = seed;
             sk.on = (k == nsteps - 1);
             k_adj_cell<<<grid, 128, 0, s>>>(ctx->dp, ctx->f[0], sr + 3 * (size_t)n * (k - k0), ctx->type, ctx->phi,
-                                              (const GrayRec *)(sg + gb * (k - k0)), lam_next, lam_cur,
+                                              (const GrayRec *)(sg + gb * (k - k0)), lam_next, v_next, lam_cur,
                                               (float *)acc.p, (double *)gacc.p, sk);
-            k_adj_finish<<<grid, 128, 0, s>>>(ctx->dp, ctx->type, lam_cur, (const float *)acc.p);
+            k_adj_finish<<<grid, 128, 0, s>>>(ctx->dp, ctx->type, v_cur, (const float *)acc.p);
             e = cudaGetLastError();
             ctx->launches += 2;
             std::swap(lam_next, lam_cur);
+            std::swap(v_next, v_cur);
         }
         if (e != cudaSuccess) rc = cuda_fail(e, "lbm_adjoint_run backward");
     }
