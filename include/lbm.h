@@ -469,7 +469,7 @@ LBM_API int lbm_launch_count(lbm_ctx *ctx, long long *count);
  *             Shan-Chen coupling of the pressure p = (rhoA+rhoB)/3 + G rhoA rhoB,
  * on `stream` (cudaStream_t, NULL = legacy default), and writes *out (host;
  * out->step is 0).  Synchronises the stream.
- * Scratch: a file-scope device array of 77,952 bytes that every GPU loading
+ * Scratch: a file-scope device array of 58,496 bytes that every GPU loading
  * this library holds until exit.  Every call resolves that array's address
  * in the context current to the calling thread (cudaGetSymbolAddress: the
  * device's primary context, a context the caller made current, a primary

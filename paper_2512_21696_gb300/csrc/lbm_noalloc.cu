@@ -9,7 +9,7 @@
 // instead of context-owned memory.
 //
 // The array is g_obs_scratch below: (OBS_MAX_BLOCKS + 1) * NOBS doubles =
-// 77,952 bytes, which every GPU that loads this library holds until the
+// 58,496 bytes, which every GPU that loads this library holds until the
 // process exits.  Host code must not use the symbol itself (on the host it
 // only names a stand-in): every call resolves the array's device address in
 // the context current to the calling thread with cudaGetSymbolAddress (a

@@ -41,7 +41,7 @@ __device__ __forceinline__ float warp_max_f(float v)
     return v;
 }
 
-__global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsArgs O,
+__global__ void __launch_bounds__(OBS_BLOCK, 3) k_obs_partial(DevParams P, ObsArgs O,
                                                            const uint8_t *__restrict__ type,
                                                            const float *__restrict__ phi,
                                                            const float *__restrict__ macro,
@@ -62,10 +62,18 @@ __global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsAr
     const bool probe = O.probe != 0;  // some cell can fall inside or outside
     // cells c0 + k stride, k < UNR, per pass: all their loads are issued before
     // any is used (the fields of solid cells are read and ignored), so a pass
-    // waits on memory once; the cells are summed in the grid-stride order
+    // waits on memory once; the cells are summed in the grid-stride order.
+    // Their coordinates advance by the stride's (x, y, z) steps with carries
+    // (no division per cell).
     constexpr int UNR = 2;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; c0 < n; c0 += UNR * stride) {
+    const int nx = P.nx, ny = P.ny;
+    const int sx = (int)(stride % nx);
+    const long long sq = stride / nx;
+    const int sy = (int)(sq % ny), sz = (int)(sq / ny);
+    const long long cstart = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int x = (int)(cstart % nx), y = (int)((cstart / nx) % ny), z = (int)(cstart / ((long long)nx * ny));
+    for (long long c0 = cstart; c0 < n; c0 += UNR * stride) {
         uint8_t tk[UNR];
         float fk[UNR][7];
 #pragma unroll
@@ -82,8 +90,16 @@ __global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsAr
 #pragma unroll
         for (int k = 0; k < UNR; ++k) {
             const uint8_t t = tk[k];
+            const int cxk = x, cyk = y, czk = z;
+            // the next cell of this thread
+            x += sx;
+            const int carx = x >= nx;
+            x -= carx ? nx : 0;
+            y += sy + carx;
+            const int cary = y >= ny;
+            y -= cary ? ny : 0;
+            z += sz + cary;
             if (t == CELL_SOLID) continue;
-            const int c = (int)(c0 + k * stride);
             // per-cell terms in FP32 (products of FP32 fields, one rounding each)
             const float ra = fk[k][0], rb = fk[k][1];
             const float u0 = fk[k][2], u1 = fk[k][3], u2 = fk[k][4];
@@ -92,21 +108,19 @@ __global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsAr
                 ++bad;
                 continue;
             }
-            const int x = c % P.nx;
             s[0] = ff_add_f(s[0], ra);
             s[1] = ff_add_f(s[1], rb);
             // saturation weight: phi in gray cells, 1 in pores, reservoirs left out
             const float phc = t == CELL_GRAY ? fk[k][6] : (t == CELL_PORE ? 1.0f : 0.0f);
             s[2] = ff_add_f(s[2], phc * sw);
             s[3] = ff_add_f(s[3], phc);
-            if (x == P.nx - 1) s[4] = ff_add_f(s[4], u0);
+            if (cxk == nx - 1) s[4] = ff_add_f(s[4], u0);
             s[5] = ff_add_f(s[5], u0);
             s[6] = ff_add_f(s[6], u1);
             s[7] = ff_add_f(s[7], u2);
             umax = fmaxf(umax, sqrtf(u0 * u0 + u1 * u1 + u2 * u2));
             if (probe) {  // uniform: the pressure probe is set
-                const int xy = c / P.nx;
-                const float dx = x - pcx, dy = xy % P.ny - pcy, dz = xy / P.ny - pcz;
+                const float dx = cxk - pcx, dy = cyk - pcy, dz = czk - pcz;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const float pr = (ra + rb) * (1.0f / 3.0f) + Gf * ra * rb;
                 if (r2 < rin2) { s[8] = ff_add_f(s[8], pr); ++cin; }
@@ -115,8 +129,8 @@ __global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsAr
         }
     }
     // warp and block levels in float-float and integers, all on the FP32
-    // pipe (a few FP64 operations per block, times 608 blocks, had kept the
-    // FP64 pipe a third busy); counts stay exact as float-float
+    // pipe (a few FP64 operations per block, times hundreds of blocks, had
+    // kept the FP64 pipe a third busy); counts stay exact as float-float
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NS; ++k) {
@@ -163,12 +177,20 @@ __global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsAr
     __threadfence();
     // warp w sums slots w, w + nw, ...: lanes over a fixed subset of the rows,
     // then the warp in a fixed order (deterministic)
+    // (a lane's rows are loaded together, then summed in row order)
+    constexpr int RPL = (OBS_MAX_BLOCKS + 31) / 32;
     for (int k = warp; k < NOBS; k += nw) {
+        float2 pv[RPL];
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int b = lane + 32 * t;
+            pv[t] = b < (int)gridDim.x ? __ldcg(&partial[(size_t)b * NOBS + k]) : make_float2(0.f, 0.f);
+        }
         ff v = {0.f, 0.f};
-        for (int b = lane; b < (int)gridDim.x; b += 32) {
-            const float2 x = __ldcg(&partial[(size_t)b * NOBS + k]);
-            if (k == SLOT_MAX) v.hi = fmaxf(v.hi, x.x);
-            else v = ff_add(v, ff{x.x, x.y});
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            if (k == SLOT_MAX) v.hi = fmaxf(v.hi, pv[t].x);
+            else v = ff_add(v, ff{pv[t].x, pv[t].y});
         }
         if (k == SLOT_MAX) v.hi = warp_max_f(v.hi);
         else v = warp_sum_ff(v);

@@ -15,7 +15,7 @@ constexpr int NOBS = 16;
 constexpr int SLOT_MAX = 8;
 constexpr int SLOT_COUNTER = 15;  // of the output row: blocks done (zero between reductions)
 constexpr int OBS_BLOCK = 256;
-constexpr int OBS_MAX_BLOCKS = 608;
+constexpr int OBS_MAX_BLOCKS = 456;  // 3 resident blocks on each of 152 SMs
 
 // Pressure probe in FP32 (the kernels do no FP64 arithmetic per thread):
 // centre, squared inner and outer radii, G; probe = 0 when no cell can fall
@@ -41,7 +41,7 @@ inline ObsArgs obs_args(const double c[3], double r_in, double r_out, double G, 
 // row of NOBS float-float partials (hi, lo) per block in `partial`; the last
 // block to finish sums the rows in a fixed order into out[NOBS] (FP64).
 // out[SLOT_COUNTER] must be zero at launch and is zero again at exit.
-__global__ void __launch_bounds__(OBS_BLOCK, 4) k_obs_partial(DevParams P, ObsArgs O, const uint8_t *__restrict__ type,
+__global__ void __launch_bounds__(OBS_BLOCK, 3) k_obs_partial(DevParams P, ObsArgs O, const uint8_t *__restrict__ type,
                               const float *__restrict__ phi, const float *__restrict__ macro,
                               float2 *__restrict__ partial, double *__restrict__ out);
 
