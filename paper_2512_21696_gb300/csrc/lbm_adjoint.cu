@@ -3,7 +3,11 @@
 // precompute, the per-cell porosity (Eqs. 1 and 4-7).
 //
 // One adjoint step (going backwards, step n):
-//   k_adj_cell   per fluid cell x: recomputes the cell's forward map in FP32
+//   k_adj_cell   per fluid cell x (one thread per entry of a list of the
+//                fluid cells, plain pore cells first, then gray cells, each
+//                in index order, so that a warp takes one branch of the
+//                gray-cell terms and no lane idles on a solid cell):
+//                recomputes the cell's forward map in FP32
 //                from the stored state of step n, takes the adjoints of its 38
 //                outputs from lam^{n+1} at their push targets (own part plus
 //                the target cell's gathered neighbour term), and runs the
@@ -111,13 +115,13 @@ __global__ void __launch_bounds__(128, 3) k_adj_cell(DevParams P, const float *_
                                                   const float *__restrict__ lam_next,
                                                   const float *__restrict__ v_next, float *__restrict__ lam_out,
                                                   float *__restrict__ contrib, double *__restrict__ gacc,
-                                                  AdjSeed seed)
+                                                  AdjSeed seed, const int *__restrict__ cells, int ncells)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ncells) return;
+    const int c = cells[e];
     const int n = P.n;
-    if (c >= n) return;
     const uint8_t t = type[c];
-    if (t == CELL_SOLID) return;
     const int x = c % P.nx, y = (c / P.nx) % P.ny, z = c / (P.nx * P.ny);
     int nb[Q];
     unsigned wall = 0;
@@ -878,6 +882,22 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
     LBM_CUDA(cudaMemsetAsync(gacc.p, 0, 8 * (size_t)n * sizeof(double), s));
     LBM_CUDA(cudaMemsetAsync(dphi.p, 0, (size_t)n * sizeof(double), s));
     const dim3 grid((n + 127) / 128);
+    // the fluid cells, plain pore (and other non-gray) cells first, then gray
+    // cells, each in index order
+    std::vector<uint8_t> ht((size_t)n);
+    LBM_CUDA(cudaMemcpyAsync(ht.data(), ctx->type, (size_t)n, cudaMemcpyDeviceToHost, s));
+    LBM_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> hl;
+    hl.reserve((size_t)n);
+    for (int pass = 0; pass < 2; ++pass)
+        for (int c = 0; c < n; ++c)
+            if (ht[c] != CELL_SOLID && ((ht[c] == CELL_GRAY) == (pass == 1))) hl.push_back(c);
+    const int ncells = (int)hl.size();
+    DevBuf cells;
+    LBM_CUDA(cudaMalloc(&cells.p, std::max<size_t>(1, hl.size()) * sizeof(int)));
+    if (ncells > 0)
+        LBM_CUDA(cudaMemcpyAsync(cells.p, hl.data(), hl.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    const dim3 grid_cells((unsigned)std::max(1, (ncells + 127) / 128));
     if (sumphi > 0)
         k_sat_weight_grad<<<grid, 128, 0, s>>>(n, ctx->type, ctx->macro, dLdS, S, sumphi, (double *)dphi.p);
     float *lam_next = (float *)lam0.p, *lam_cur = (float *)lam1.p;
@@ -906,9 +926,10 @@ extern "C" int lbm_adjoint_run(lbm_ctx *ctx, const lbm_loss *L, int nsteps, int 
             ctx->cur = 0;
             AdjSeed sk = seed;
             sk.on = (k == nsteps - 1);
-            k_adj_cell<<<grid, 128, 0, s>>>(ctx->dp, ctx->f[0], sr + 3 * (size_t)n * (k - k0), ctx->type, ctx->phi,
-                                              (const GrayRec *)(sg + gb * (k - k0)), lam_next, v_next, lam_cur,
-                                              (float *)acc.p, (double *)gacc.p, sk);
+            k_adj_cell<<<grid_cells, 128, 0, s>>>(ctx->dp, ctx->f[0], sr + 3 * (size_t)n * (k - k0), ctx->type,
+                                                    ctx->phi, (const GrayRec *)(sg + gb * (k - k0)), lam_next, v_next,
+                                                    lam_cur, (float *)acc.p, (double *)gacc.p, sk,
+                                                    (const int *)cells.p, ncells);
             k_adj_finish<<<grid, 128, 0, s>>>(ctx->dp, ctx->type, v_cur, (const float *)acc.p);
             e = cudaGetLastError();
             ctx->launches += 2;
