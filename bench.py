@@ -69,8 +69,9 @@ def fiber_inputs(edge=192, axis=0):
 def algorithmic_bytes(cell):
     """Bytes each kernel must move per launch: 304 B per fluid cell (two
     components x 19 FP32 populations, read and written), 1 B cell type per
-    cell and 25 B per gray cell (porosity, principal axis, residual state);
-    per-kernel figures count what each kernel itself reads."""
+    cell and 25 B per gray cell (porosity, principal axis, residual state;
+    the kernels' own gray record is 32 B, but the figure is the method's);
+    the two-launch kernels add the 8 B of densities they exchange."""
     n = cell.size
     fluid = int((cell != 1).sum())
     gray = int((cell == 2).sum())
@@ -78,10 +79,10 @@ def algorithmic_bytes(cell):
     return dict(step=step,
                 step_lp=fluid * 152 + n * 1 + gray * 25,
                 step_r16=fluid * 160 + n * 1 + gray * 25,
-                k_fused=fluid * 304 + n * 1 + gray * 32,
+                k_fused=fluid * 304 + n * 1 + gray * 25,
                 k_march=fluid * 304 + n * 1 + gray * 25,
-                k_fused_lp=fluid * 152 + n * 1 + gray * 32,
-                k_collide=fluid * 304 + n * 1 + n * 8 + gray * 32,
+                k_fused_lp=fluid * 152 + n * 1 + gray * 25,
+                k_collide=fluid * 304 + n * 1 + n * 8 + gray * 25,
                 k_density=fluid * 152 + n * 1 + n * 8), fluid, gray
 
 
