@@ -3,18 +3,22 @@
 //
 // Each CTA owns an x-y tile of TX x TY columns and marches along z over a
 // chunk of planes.  Two shared-memory rings follow the march:
-//   raw  (3 planes, tile + 2-cell halo): cell type and fixed-point rest
+//   raw  (4 planes, tile + 2-cell halo): cell type and fixed-point rest
 //        populations, the reference of every arrived population;
-//   den  (3 planes, tile + 1-cell halo): rest populations, drho, type and
+//   den  (4 planes, tile + 1-cell halo): rest populations, drho, type and
 //        global index of the current time level, the source of the density
 //        stencils (gradients, Atwood number, Eq. 4 Hessian) and of the push
 //        targets.
 // With lead plane L the pipeline per iteration is
-//   phase 0  raw plane L+1 from HBM
-//   phase 1  drho of the den region at plane L (own slots from HBM/L2, source
-//            rest populations from the raw ring)
-//   phase 3  forces + collision of the tile at plane L-1 (own slots again,
+//   phase A  raw plane L+2 from HBM, and drho of the den region at plane L
+//            (own slots from HBM/L2, source rest populations from the raw
+//            ring)
+//   barrier
+//   phase B  forces + collision of the tile at plane L-1 (own slots again,
 //            from L2), push of the new populations into the neighbours' slots.
+// The rings hold four planes, so one barrier per plane suffices: a warp may
+// still be in phase B of plane L-1 while others run phase A of plane L+1,
+// and every slot phase A writes was last read before the previous barrier.
 // All per-cell arithmetic is shared with the two-launch path
 // (lbm_cell.cuh), so both give identical states.
 #pragma once
@@ -40,9 +44,10 @@ struct Tiles {
     static constexpr int NT = TX * TY;
     static constexpr int RX = TX + 4, RY = TY + 4, RN = RX * RY;
     static constexpr int DX = TX + 2, DY = TY + 2, DN = DX * DY;
+    static constexpr int NP = 4;  // planes per ring
     static constexpr size_t smem()
     {
-        return 3 * RN * sizeof(RawCell) + 3 * DN * (sizeof(DenCell) + sizeof(DenMeta) + sizeof(float));
+        return NP * RN * sizeof(RawCell) + NP * DN * (sizeof(DenCell) + sizeof(DenMeta) + sizeof(float));
     }
 };
 
@@ -53,7 +58,8 @@ __device__ __forceinline__ int wrap_coord(int v, int n, int per)
     v %= n;
     return v < 0 ? v + n : v;
 }
-__device__ __forceinline__ int ring3(int p) { return ((p % 3) + 3) % 3; }
+// slot of plane p in a four-plane ring (also for negative p: two's complement)
+__device__ __forceinline__ int ring4(int p) { return p & 3; }
 
 // One work item: the TX x TY columns at (x0, y0) over planes [za, zb) of the
 // lattice of shape G (G.n is the slot stride of ly, type, gray and macro),
@@ -70,10 +76,11 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
                                            int za, int zb, unsigned char *smem_raw, float *__restrict__ cap = nullptr)
 {
     using T = Tiles<TX, TY>;
-    RawCell *raw = reinterpret_cast<RawCell *>(smem_raw);         // [3][RN]
-    DenCell *den = reinterpret_cast<DenCell *>(raw + 3 * T::RN);  // [3][DN]
-    DenMeta *dmeta = reinterpret_cast<DenMeta *>(den + 3 * T::DN); // [3][DN]
-    float *dat = reinterpret_cast<float *>(dmeta + 3 * T::DN);     // [3][DN] Atwood number
+    constexpr int NP = T::NP;
+    RawCell *raw = reinterpret_cast<RawCell *>(smem_raw);          // [NP][RN]
+    DenCell *den = reinterpret_cast<DenCell *>(raw + NP * T::RN);  // [NP][DN]
+    DenMeta *dmeta = reinterpret_cast<DenMeta *>(den + NP * T::DN); // [NP][DN]
+    float *dat = reinterpret_cast<float *>(dmeta + NP * T::DN);     // [NP][DN] Atwood number
     const int n = G.n;
     const int tid = threadIdx.x;
 
@@ -97,18 +104,18 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
         return rc;
     };
     auto load_raw = [&](int q) {
-        RawCell *dst = raw + ring3(q) * T::RN;
+        RawCell *dst = raw + ring4(q) * T::RN;
         for (int e = tid; e < T::RN; e += T::NT) dst[e] = raw_entry(q, e);
     };
 
     // ---- phase 1: drho of the den region (tile + 1-cell halo) at plane L ----
     auto densities = [&](int L) {
-        const RawCell *r0 = raw + ring3(L - 1) * T::RN;
-        const RawCell *r1 = raw + ring3(L) * T::RN;
-        const RawCell *r2 = raw + ring3(L + 1) * T::RN;
-        DenCell *dd = den + ring3(L) * T::DN;
-        DenMeta *dm = dmeta + ring3(L) * T::DN;
-        float *da = dat + ring3(L) * T::DN;
+        const RawCell *r0 = raw + ring4(L - 1) * T::RN;
+        const RawCell *r1 = raw + ring4(L) * T::RN;
+        const RawCell *r2 = raw + ring4(L + 1) * T::RN;
+        DenCell *dd = den + ring4(L) * T::DN;
+        DenMeta *dm = dmeta + ring4(L) * T::DN;
+        float *da = dat + ring4(L) * T::DN;
         const int gz = wrap_coord(L, G.nz, P.per[2]);
         for (int e = tid; e < T::DN; e += T::NT) {
             const int dx = e % T::DX, dy = e / T::DX;
@@ -159,15 +166,15 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
     auto collide = [&](int z) {
         const int ux = tid % TX, uy = tid / TX;
         if (x0 + ux >= G.nx || y0 + uy >= G.ny) return;
-        const DenCell *d0p = den + ring3(z - 1) * T::DN;
-        const DenCell *d1 = den + ring3(z) * T::DN;
-        const DenCell *d2 = den + ring3(z + 1) * T::DN;
-        const DenMeta *m0 = dmeta + ring3(z - 1) * T::DN;
-        const DenMeta *m1 = dmeta + ring3(z) * T::DN;
-        const DenMeta *m2 = dmeta + ring3(z + 1) * T::DN;
-        const float *a0 = dat + ring3(z - 1) * T::DN;
-        const float *a1 = dat + ring3(z) * T::DN;
-        const float *a2 = dat + ring3(z + 1) * T::DN;
+        const DenCell *d0p = den + ring4(z - 1) * T::DN;
+        const DenCell *d1 = den + ring4(z) * T::DN;
+        const DenCell *d2 = den + ring4(z + 1) * T::DN;
+        const DenMeta *m0 = dmeta + ring4(z - 1) * T::DN;
+        const DenMeta *m1 = dmeta + ring4(z) * T::DN;
+        const DenMeta *m2 = dmeta + ring4(z + 1) * T::DN;
+        const float *a0 = dat + ring4(z - 1) * T::DN;
+        const float *a1 = dat + ring4(z) * T::DN;
+        const float *a2 = dat + ring4(z + 1) * T::DN;
         const int dk = (ux + 1) + T::DX * (uy + 1);
         const DenMeta me = m1[dk];
         if (me.type == CELL_SOLID) {
@@ -251,9 +258,10 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
 
     load_raw(za - 2);
     load_raw(za - 1);
+    load_raw(za);
+    __syncthreads();
     for (int L = za - 1; L <= zb; ++L) {
-        load_raw(L + 1);
-        __syncthreads();
+        if (L + 2 <= zb + 1) load_raw(L + 2);
         densities(L);
         __syncthreads();
         if (L - 1 >= za) collide(L - 1);
