@@ -27,7 +27,7 @@ template <int TX, int TY>
 struct TilesLP {
     static constexpr int NT = TX * TY;
     static constexpr int DX = TX + 2, DY = TY + 2, DN = DX * DY;
-    static constexpr size_t smem() { return 3 * DN * (sizeof(DenLP) + sizeof(int)); }
+    static constexpr size_t smem() { return 4 * DN * (sizeof(DenLP) + sizeof(int)); }  // four-plane ring
 };
 
 __device__ __forceinline__ int wrap_lp(int v, int n, int per)
@@ -37,7 +37,8 @@ __device__ __forceinline__ int wrap_lp(int v, int n, int per)
     v %= n;
     return v < 0 ? v + n : v;
 }
-__device__ __forceinline__ int ring3_lp(int p) { return ((p % 3) + 3) % 3; }
+// slot of plane p in the four-plane ring (also for negative p: two's complement)
+__device__ __forceinline__ int ring4_lp(int p) { return p & 3; }
 
 template <int TX, int TY, int MINB, bool MACRO, class H>
 __global__ void __launch_bounds__(TX *TY, MINB)
@@ -46,8 +47,8 @@ __global__ void __launch_bounds__(TX *TY, MINB)
 {
     using T = TilesLP<TX, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    DenLP *den = reinterpret_cast<DenLP *>(smem_raw);        // [3][DN]
-    int *dgi = reinterpret_cast<int *>(den + 3 * T::DN);     // [3][DN] global index (-1 solid)
+    DenLP *den = reinterpret_cast<DenLP *>(smem_raw);        // [4][DN]
+    int *dgi = reinterpret_cast<int *>(den + 4 * T::DN);     // [4][DN] global index (-1 solid)
 
     const int n = P.n;
     const int tid = threadIdx.x;
@@ -63,8 +64,8 @@ __global__ void __launch_bounds__(TX *TY, MINB)
 
         // densities of every den cell (tile + 1-cell halo) at plane L
         auto densities = [&](int L) {
-            DenLP *dd = den + ring3_lp(L) * T::DN;
-            int *dg = dgi + ring3_lp(L) * T::DN;
+            DenLP *dd = den + ring4_lp(L) * T::DN;
+            int *dg = dgi + ring4_lp(L) * T::DN;
             const int gz = wrap_lp(L, P.nz, P.per[2]);
             for (int e = tid; e < T::DN; e += T::NT) {
                 const int gx = wrap_lp(x0 - 1 + e % T::DX, P.nx, P.per[0]);
@@ -95,12 +96,12 @@ __global__ void __launch_bounds__(TX *TY, MINB)
         auto collide = [&](int z) {
             const int ux = tid % TX, uy = tid / TX;
             if (x0 + ux >= P.nx || y0 + uy >= P.ny) return;
-            const DenLP *d0p = den + ring3_lp(z - 1) * T::DN;
-            const DenLP *d1 = den + ring3_lp(z) * T::DN;
-            const DenLP *d2 = den + ring3_lp(z + 1) * T::DN;
-            const int *g0 = dgi + ring3_lp(z - 1) * T::DN;
-            const int *g1 = dgi + ring3_lp(z) * T::DN;
-            const int *g2 = dgi + ring3_lp(z + 1) * T::DN;
+            const DenLP *d0p = den + ring4_lp(z - 1) * T::DN;
+            const DenLP *d1 = den + ring4_lp(z) * T::DN;
+            const DenLP *d2 = den + ring4_lp(z + 1) * T::DN;
+            const int *g0 = dgi + ring4_lp(z - 1) * T::DN;
+            const int *g1 = dgi + ring4_lp(z) * T::DN;
+            const int *g2 = dgi + ring4_lp(z + 1) * T::DN;
             const int dk = (ux + 1) + T::DX * (uy + 1);
             const DenLP me = d1[dk];
             if (me.type == CELL_SOLID) {
@@ -163,13 +164,16 @@ __global__ void __launch_bounds__(TX *TY, MINB)
             collide_store<MACRO>(P, acc, held ? 0.f : P.mss, t, c, n, st, M, gf, gAt, csf, hA, hB, gray, macro, tgt);
         };
 
+        // one barrier per plane: the densities of plane L+1 go into the slot
+        // of plane L-3, which the collision of plane L-2 read before the
+        // barrier of plane L
         densities(za - 1);
         for (int L = za; L <= zb; ++L) {
             densities(L);
             __syncthreads();
             if (L - 1 >= za) collide(L - 1);
-            __syncthreads();
         }
+        __syncthreads();  // the ring is reused by the next item
     }
 }
 
