@@ -84,7 +84,7 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
     const int n = G.n;
     const int tid = threadIdx.x;
 
-    // ---- phase 0: raw plane q (tile + 2-cell halo) ----
+    // ---- phase A, first part: raw plane q (tile + 2-cell halo) ----
     auto raw_entry = [&](int q, int e) -> RawCell {
         const int gz = wrap_coord(q, G.nz, P.per[2]);
         const int rx = e % T::RX, ry = e / T::RX;
@@ -108,7 +108,7 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
         for (int e = tid; e < T::RN; e += T::NT) dst[e] = raw_entry(q, e);
     };
 
-    // ---- phase 1: drho of the den region (tile + 1-cell halo) at plane L ----
+    // ---- phase A: drho of the den region (tile + 1-cell halo) at plane L ----
     auto densities = [&](int L) {
         const RawCell *r0 = raw + ring4(L - 1) * T::RN;
         const RawCell *r1 = raw + ring4(L) * T::RN;
@@ -162,7 +162,7 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
         }
     };
 
-    // ---- phase 3: forces + collision of the tile at plane z ----
+    // ---- phase B: forces + collision of the tile at plane z ----
     auto collide = [&](int z) {
         const int ux = tid % TX, uy = tid / TX;
         if (x0 + ux >= G.nx || y0 + uy >= G.ny) return;

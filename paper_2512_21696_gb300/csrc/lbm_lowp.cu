@@ -6,11 +6,11 @@
 // the one of the F32 kernel with a single ring: the populations are absolute
 // (shifted by a constant), so a cell needs no rest population of its
 // sources.
-//   den ring (3 planes, tile + 1-cell halo): rho^A, rho^B, type, global index
+//   den ring (4 planes, tile + 1-cell halo): rho^A, rho^B, type, global index
 //   and the Atwood number of the current time level.
 // Per iteration with lead plane L: densities of the den region at plane L,
-// then forces + collision of the tile at plane L - 1 (own slots again, from
-// L2) with the push of the new populations.
+// one barrier, then forces + collision of the tile at plane L - 1 (own slots
+// again, from L2) with the push of the new populations.
 #include <algorithm>
 
 #include "lbm_cell.cuh"
