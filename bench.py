@@ -97,7 +97,7 @@ def measured_peak():
 
 # The sources that define the fused step kernel: a committed ncu summary's
 # traffic figure is used only while these are unchanged since its capture.
-KERNEL_SOURCES = ("lbm_cell.cuh", "lbm_common.cuh", "lbm_fused.cu", "lbm_fused.cuh")
+KERNEL_SOURCES = ("lbm_cell.cuh", "lbm_common.cuh", "lbm_fused.cu", "lbm_fused.cuh", "lbm_fused_launch.cuh")
 
 
 def kernel_source_hash():
@@ -319,9 +319,9 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "frac_of_nominal_8tbs": round(achieved / 8000.0, 4),
-                     # the committed capture is of the F32 drainage launch
+                     # the committed capture is of the F32 drainage launch with the default tile
                      "traffic": ncu_traffic(dname) if (args.storage == "f32" and args.workload == "drainage"
-                                                       and args.path == 0 and args.tile == 2) else None,
+                                                       and args.path == 0 and args.tile == 8) else None,
                      "alg_bytes_per_launch": alg.get(dkey, alg[step_key]),
                      "avg_launch_ms": round(avg_s * 1e3, 5)},
         "mflups": round(job_mlups(fluid, args.steps, world, ms), 2),  # non-solid cells only
@@ -997,9 +997,10 @@ def main():
                     help="rev: after timing, step every run to steady flow (at most this many steps); revlib: drive "
                          "every two-phase run to its target Sw with the mass-sink-source controller, then to steady "
                          "flow, before the timed steps (at most this many steps each)")
-    ap.add_argument("--tile", type=int, default=2,
+    ap.add_argument("--tile", type=int, default=8,
                     help="fused tile: 0 = 32x8, 1 = 32x16, 2 = 32x8 two CTAs/SM, 3 = 32x12, 4 = 64x8, "
-                         "5 / 6 = published-density march 32x8 / 32x7")
+                         "5 / 6 = published-density march 32x8 / 32x7, 7 = 64x7, "
+                         "8 = chosen per grid among 2, 4, 7 (default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

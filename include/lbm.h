@@ -347,12 +347,15 @@ LBM_API int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *c
  * (rolling z-window with shared-memory halos), path 1 = two launches
  * (densities, then forces + collision).  tile selects the fused tile:
  * 0 = 32x8 columns, 1 = 32x16, 2 = 32x8 with two CTAs per SM, 3 = 32x12,
- * 4 = 64x8, 5 and 6 = the published-density march on 32x8 and 32x7 tiles
+ * 4 = 64x8, 7 = 64x7, 8 = chosen per grid among 2, 4 and 7 (the one whose
+ * z-chunked columns best fill the resident CTA slots; 4 and 7 only where nx
+ * is a multiple of 64; 16-bit storages run 2), 5 and 6 = the
+ * published-density march on 32x8 and 32x7 tiles
  * (every CTA resident, one cooperative launch per step: each tile publishes
  * its densities and reads its ring from its neighbours instead of
  * recomputing it; no CUDA-graph replay).  The march runs the plain F32 step;
  * with reservoir cells, a mass-sink-source rate, a 16-bit storage or more
- * tile columns than resident CTAs, tiles 5 and 6 run tile 2.  Default: 2.
+ * tile columns than resident CTAs, tiles 5 and 6 run tile 2.  Default: 8.
  * Both paths and all tiles compute
  * identical states.  A march whose bounded wait for a neighbouring tile gave
  * up (1 s) makes the next lbm_observables or lbm_get_fields return

@@ -807,7 +807,7 @@ int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *count)
 
 int lbm_set_kernel(lbm_ctx *ctx, int path, int tile)
 {
-    if (!ctx || path < 0 || path > 1 || tile < 0 || tile > 6) return LBM_ERR_ARG;
+    if (!ctx || path < 0 || path > 1 || tile < 0 || tile > 8) return LBM_ERR_ARG;
     ctx->path = path;
     ctx->tile = tile;
     lbm::drop_graphs(ctx);

@@ -41,7 +41,8 @@ struct lbm_ctx {
     int prog_len = 0;
 
     int path = 0;   // 0: fused single launch, 1: two launches (density, collide)
-    int tile = 2;   // fused tile variant (lbm_set_kernel); 2 = 32x8, two CTAs per SM; 5, 6 = the march
+    int tile = 8;   // fused tile variant (lbm_set_kernel); 8 = automatic among 2, 4, 7; 5, 6 = the march
+    int auto_tile = -1;  // the automatic choice, once made (depends on the grid only)
     bool has_geometry = false;
     bool has_fields = false;
     bool view = false;  // a run of a batch: buffers owned by the batch

@@ -52,8 +52,9 @@ def _compare_static(case, gstat, ostat):
     np.testing.assert_allclose(sores[gray], ostat["sores"][gray], rtol=2e-6, atol=1e-7)
 
 
-# (path, tile): fused tiles 0-4, the published-density march (5, 6), two launches
-KERNELS = [(0, 0), (0, 1), (0, 2), (0, 3), (0, 4), (0, 5), (0, 6), (1, 0)]
+# (path, tile): fused tiles 0-4 and 7, the published-density march (5, 6), the
+# automatic choice (8), two launches
+KERNELS = [(0, 0), (0, 1), (0, 2), (0, 3), (0, 4), (0, 5), (0, 6), (0, 7), (0, 8), (1, 0)]
 
 
 @pytest.mark.parametrize("path,tile", KERNELS)
@@ -357,6 +358,28 @@ def test_march_is_bit_identical_to_rolling_window(shape, periodic, steps, tile):
     a, ga, _ = LC.run_gpu(case, steps, path=0, tile=tile)
     b, gb, _ = LC.run_gpu(case, steps, path=0, tile=2)
     assert ga["nan_count"] == 0 and gb["nan_count"] == 0  # equal arrays of NaN would compare equal
+    for x, y in zip(a, b):
+        assert np.all(np.isfinite(y))
+        np.testing.assert_array_equal(x, y)
+    assert ga == gb
+
+
+@pytest.mark.parametrize("tile", [4, 7, 8])
+@pytest.mark.parametrize("shape,periodic,steps", [((48, 48, 48), (1, 1, 1), 25), ((40, 37, 70), (1, 0, 1), 12),
+                                                  ((9, 6, 11), (0, 1, 0), 12), ((128, 128, 128), (1, 1, 1), 3),
+                                                  ((8, 192, 192), (1, 1, 1), 6)])
+def test_tile_shapes_are_bit_identical(shape, periodic, steps, tile):
+    """The 64-wide tiles (64x8, 64x7 with a ragged last band of rows) and the
+    automatic choice among the tile shapes compute the default tile's
+    states bit for bit (fields and observables), on lattices where the
+    choice falls on different shapes."""
+    if shape[0] == shape[1] == shape[2]:
+        case = LC.drainage(shape[0])
+    else:
+        case = LC.mixed_features(shape=shape, periodic=periodic, seed=sum(shape))
+    a, ga, _ = LC.run_gpu(case, steps, path=0, tile=tile)
+    b, gb, _ = LC.run_gpu(case, steps, path=0, tile=2)
+    assert ga["nan_count"] == 0 and gb["nan_count"] == 0
     for x, y in zip(a, b):
         assert np.all(np.isfinite(y))
         np.testing.assert_array_equal(x, y)

@@ -16,7 +16,7 @@ from paper_2512_21696_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
-KERNELS = [(0, 0), (0, 1), (0, 2), (0, 3), (0, 4), (1, 0)]  # (path, tile): fused tiles 0-4, two launches
+KERNELS = [(0, 0), (0, 1), (0, 2), (0, 3), (0, 4), (0, 7), (0, 8), (1, 0)]  # (path, tile): fused tiles, two launches
 
 
 def _errs(case, gpu, orc):
