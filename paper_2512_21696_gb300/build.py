@@ -15,7 +15,8 @@ REPO = os.path.dirname(PKG_DIR)
 CSRC = os.path.join(PKG_DIR, "csrc")
 OUT_DIR = os.path.join(PKG_DIR, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_step.cu", "lbm_geom.cu", "lbm_obs.cu", "lbm_noalloc.cu", "lbm_fused.cu", "lbm_fused_alt.cu", "lbm_march.cu",
+SOURCES = ["lbm_api.cu", "lbm_step.cu", "lbm_geom.cu", "lbm_obs.cu", "lbm_noalloc.cu", "lbm_fused.cu", "lbm_fused_alt.cu", "lbm_fused_f16r.cu",
+           "lbm_fused_bf16r.cu", "lbm_march.cu",
            "lbm_lowp.cu", "lbm_batch.cu", "lbm_adjoint.cu", "lbm_d2q9.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

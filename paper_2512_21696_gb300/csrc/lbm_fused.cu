@@ -52,7 +52,7 @@ static int auto_tile(lbm_ctx *ctx)
 // (128 registers), 2 = 32x8 with two CTAs per SM (128 registers), 3 = 32x12
 // (168 registers), 4 = 64x8 (128 registers), 7 = 64x7 (one CTA per SM),
 // 8 = the automatic choice above (the default).
-// The rest-referenced 16-bit layouts run tile 2.
+// The rest-referenced 16-bit layouts run tiles 2, 4 and 7 (others run 2).
 cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro)
 {
     if (ctx->rho_cap) {  // the adjoint's replay: plain F32 steps that also store their densities
@@ -66,14 +66,12 @@ cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro)
         const cudaError_t e = launch_march(ctx, write_macro, &ran);
         if (e != cudaSuccess || ran) return e;
     }
-    if (ctx->p.storage == LBM_STORAGE_F16R)
-        return launch_fused_tile<32, 8, 2>(ctx, write_macro, lay_r16<LayF16R>(ctx, ctx->cur, 1 - ctx->cur));
-    if (ctx->p.storage == LBM_STORAGE_BF16R)
-        return launch_fused_tile<32, 8, 2>(ctx, write_macro, lay_r16<LayB16R>(ctx, ctx->cur, 1 - ctx->cur));
-    const LayF32 ly{ctx->f[ctx->cur], ctx->f[1 - ctx->cur], ctx->n};
     int tile = ctx->tile;
     if (tile == 8) tile = auto_tile(ctx);
     else if (tile == 5 || tile == 6) tile = 2;  // where the march does not apply
+    if (ctx->p.storage == LBM_STORAGE_F16R) return launch_fused_f16r(ctx, tile, write_macro);
+    if (ctx->p.storage == LBM_STORAGE_BF16R) return launch_fused_bf16r(ctx, tile, write_macro);
+    const LayF32 ly{ctx->f[ctx->cur], ctx->f[1 - ctx->cur], ctx->n};
     switch (tile) {
     case 2: return launch_fused_tile<32, 8, 2>(ctx, write_macro, ly);
     case 4: return launch_fused_tile<64, 8, 1>(ctx, write_macro, ly);

@@ -1,7 +1,8 @@
 // The fused step kernel of one lattice and its launch, shared by the
 // translation units that instantiate its tile shapes (lbm_fused.cu: the
 // default shapes and the automatic choice; lbm_fused_alt.cu: the other
-// selectable shapes, compiled in parallel).
+// selectable shapes; lbm_fused_f16r.cu, lbm_fused_bf16r.cu: the 16-bit
+// rest-referenced layouts; compiled in parallel).
 //
 // Work items are (column, z-chunk) with the items of one chunk consecutive, so
 // the CTAs of a wave march neighbouring columns through the same planes at the
@@ -103,5 +104,18 @@ static cudaError_t launch_fused_tile(lbm_ctx *ctx, bool write_macro, LY ly)
 
 // Tiles 0 (32x8, one CTA per SM), 1 (32x16) and 3 (32x12), in lbm_fused_alt.cu.
 cudaError_t launch_fused_alt(lbm_ctx *ctx, int tile, bool write_macro, const LayF32 &ly);
+// The rest-referenced 16-bit layouts on tiles 2, 4 and 7 (any other tile runs
+// 2), one translation unit per layout (lbm_fused_f16r.cu, lbm_fused_bf16r.cu).
+template <class LY>
+static cudaError_t launch_r16_tile(lbm_ctx *ctx, int tile, bool write_macro, LY ly)
+{
+    switch (tile) {
+    case 4: return launch_fused_tile<64, 8, 1>(ctx, write_macro, ly);
+    case 7: return launch_fused_tile<64, 7, 1>(ctx, write_macro, ly);
+    default: return launch_fused_tile<32, 8, 2>(ctx, write_macro, ly);
+    }
+}
+cudaError_t launch_fused_f16r(lbm_ctx *ctx, int tile, bool write_macro);
+cudaError_t launch_fused_bf16r(lbm_ctx *ctx, int tile, bool write_macro);
 
 }  // namespace lbm

@@ -107,3 +107,19 @@ def test_lowp_checkpoint_roundtrip(storage, cell_bytes):
             np.testing.assert_array_equal(x, y)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("storage", [3, 4])
+@pytest.mark.parametrize("tile", [4, 7, 8])
+@pytest.mark.parametrize("n,steps", [(48, 20), (128, 3)])
+def test_rest_referenced_tile_shapes_are_bit_identical(storage, tile, n, steps):
+    """F16R / BF16R on the 64-wide tiles and the automatic choice compute the
+    32x8 tile's states bit for bit (fields and observables)."""
+    case = LC.drainage(n)
+    a, ga, _ = LC.run_gpu(case, steps, storage=storage, tile=tile)
+    b, gb, _ = LC.run_gpu(case, steps, storage=storage, tile=2)
+    assert ga["nan_count"] == 0 and gb["nan_count"] == 0
+    for x, y in zip(a, b):
+        assert np.all(np.isfinite(y))
+        np.testing.assert_array_equal(x, y)
+    assert ga == gb
