@@ -95,9 +95,10 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-# The sources that define the fused step kernel: a committed ncu summary's
-# traffic figure is used only while these are unchanged since its capture.
-KERNEL_SOURCES = ("lbm_cell.cuh", "lbm_common.cuh", "lbm_fused.cu", "lbm_fused.cuh", "lbm_fused_launch.cuh")
+# The sources that define the fused step kernel, its launch configuration and
+# the per-grid tile choice: a committed ncu summary's traffic figure is used
+# only while these are unchanged since its capture.
+KERNEL_SOURCES = ("lbm_cell.cuh", "lbm_common.cuh", "lbm_fused.cuh", "lbm_fused_launch.cuh")
 
 
 def kernel_source_hash():
@@ -228,6 +229,7 @@ def run_ours(args, rank, world, local_rank):
     p = lbm.lbm_default_params(nx, ny, nz, stream=stream.cuda_stream, storage=STORAGE_IDS[args.storage], **settings)
     ctx = lbm.lbm_create(p)
     lbm.lbm_set_kernel(ctx, args.path, args.tile)
+    _, tile_used = lbm.lbm_get_kernel(ctx)
     lbm.lbm_set_constitutive(ctx, 0, lbm.lbm_default_constitutive(**constitutive))
     dev = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in inp.items()}
     lbm.lbm_set_geometry(ctx, dev["cell"], dev["phi"], dev["ptype"])
@@ -315,7 +317,8 @@ def run_ours(args, rank, world, local_rank):
                    "storage": args.storage, "cells": n, "fluid_frac": round(fluid / n, 4),
                    "gray_frac": round(gray / n, 4), "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (2 x 319 MB population buffers)",
-                   "kernels_per_step": round(launches / args.steps, 3)},
+                   "kernels_per_step": round(launches / args.steps, 3),
+                   "path": args.path, "tile": {"requested": args.tile, "in_use": tile_used}},
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "frac_of_nominal_8tbs": round(achieved / 8000.0, 4),

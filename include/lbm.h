@@ -363,6 +363,14 @@ LBM_API int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *c
  * LBM_ERR_TIMEOUT.  LBM_ERR_ARG on unknown values. */
 LBM_API int lbm_set_kernel(lbm_ctx *ctx, int path, int tile);
 
+/* The kernel path and the fused tile a step of ctx runs (*path, *tile: host
+ * ints): tile 8 resolved to the shape chosen for this grid (2, 4 or 7), a
+ * shape the storage does not have reported as the 2 it runs; on path 1 the
+ * requested tile.  Tiles 5 and 6 are reported as requested (whether the march
+ * applies is decided per launch).  Resolves the launch configurations on the
+ * device on first use; no device work.  LBM_ERR_ARG on NULL pointers. */
+LBM_API int lbm_get_kernel(lbm_ctx *ctx, int *path, int *tile);
+
 /* Testing hook for the error path of lbm_step (no counterpart in the paper):
  * the next count step launches are issued with a zero-size thread block, a
  * configuration the CUDA runtime rejects on the host before any device work.

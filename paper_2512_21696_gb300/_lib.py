@@ -92,7 +92,7 @@ EXPORTS = [
     "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_run", "lbm_batch_step", "lbm_batch_tune", "lbm_batch_info",
     "lbm_adjoint_run", "lbm_batch_observables", "lbm_batch_step_to_steady", "lbm_set_pressure",
     "lbm_pressure_levels", "lbm_set_mss", "lbm_mss_to_saturation", "lbm_batch_mss_to_saturation",
-    "lbm_observables_async", "lbm_obs_decode", "lbm_inject_launch_failures",
+    "lbm_observables_async", "lbm_obs_decode", "lbm_inject_launch_failures", "lbm_get_kernel",
 ]
 LBM_OBS_RAW = 17
 
@@ -141,6 +141,7 @@ def load(build_if_needed: bool = True):
         lib.lbm_observables_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_double,
                                                 C.POINTER(C.c_double), vp, C.POINTER(lbm_obs)]
         lib.lbm_set_kernel.argtypes = [P, C.c_int, C.c_int]
+        lib.lbm_get_kernel.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         lib.lbm_inject_launch_failures.argtypes = [P, C.c_int]
         lib.lbm_set_pressure.argtypes = [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         lib.lbm_set_mss.argtypes = [P, C.c_double]

@@ -814,6 +814,16 @@ int lbm_set_kernel(lbm_ctx *ctx, int path, int tile)
     return LBM_OK;
 }
 
+int lbm_get_kernel(lbm_ctx *ctx, int *path, int *tile)
+{
+    if (!ctx || !path || !tile) return LBM_ERR_ARG;
+    DeviceGuard g(ctx->dev);
+    if (!g.ok) return LBM_ERR_CUDA;
+    *path = ctx->path;
+    *tile = ctx->path == 0 ? lbm::fused_tile_in_use(ctx) : ctx->tile;
+    return LBM_OK;
+}
+
 int lbm_inject_launch_failures(lbm_ctx *ctx, int count)
 {
     if (!ctx || count < 0) return LBM_ERR_ARG;

@@ -22,6 +22,7 @@ __all__ = [
     "lbm_destroy", "lbm_set_constitutive", "lbm_set_geometry", "lbm_init_fields", "lbm_step",
     "lbm_observables", "lbm_get_fields", "lbm_get_static", "lbm_save_state", "lbm_load_state",
     "lbm_profile", "lbm_profile_read", "lbm_launch_count", "lbm_abi_version", "lbm_observables_noalloc", "lbm_set_kernel",
+    "lbm_get_kernel",
     "lbm_set_pressure", "lbm_pressure_levels", "LBM_CELL_INLET", "LBM_CELL_OUTLET", "lbm_set_mss",
     "lbm_mss_to_saturation", "lbm_batch_mss_to_saturation", "lbm_observables_async", "lbm_obs_decode",
     "LBM_OBS_RAW",
@@ -314,10 +315,18 @@ def lbm_profile_read(ctx: LbmContext) -> dict:
     return {arr[k].name.decode(): (arr[k].launches, arr[k].total_ms) for k in range(min(cnt.value, 32))}
 
 
-def lbm_set_kernel(ctx: LbmContext, path: int = 0, tile: int = 0) -> None:
+def lbm_set_kernel(ctx: LbmContext, path: int = 0, tile: int = 8) -> None:
     """Kernel path of lbm_step: 0 fused (default), 1 two launches; fused tile 0 = 32x8, 1 = 32x16,
-    2 = 32x8 two CTAs per SM, 3 = 32x12, 4 = 64x8, 5 / 6 = the published-density march (32x8 / 32x7)."""
+    2 = 32x8 two CTAs per SM, 3 = 32x12, 4 = 64x8, 5 / 6 = the published-density march (32x8 / 32x7),
+    7 = 64x7, 8 = chosen per grid among 2, 4 and 7 (default)."""
     _check(L.load().lbm_set_kernel(ctx.handle, int(path), int(tile)), "lbm_set_kernel")
+
+
+def lbm_get_kernel(ctx: LbmContext) -> tuple:
+    """(path, tile) a step of ctx runs, with tile 8 resolved to the shape chosen for the grid."""
+    path, tile = C.c_int(), C.c_int()
+    _check(L.load().lbm_get_kernel(ctx.handle, C.byref(path), C.byref(tile)), "lbm_get_kernel")
+    return path.value, tile.value
 
 
 def lbm_inject_launch_failures(ctx: LbmContext, count: int) -> None:
