@@ -83,6 +83,24 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
     float *dat = reinterpret_cast<float *>(dmeta + NP * T::DN);     // [NP][DN] Atwood number
     const int n = G.n;
     const int tid = threadIdx.x;
+    // The den region has more entries than the tile has threads; the entries
+    // beyond the first pass go first to the warps of the SM sub-partitions
+    // that hold fewer of the collision's warps (warp w runs on partition
+    // w % 4): with 14 warps the collision puts 4, 4, 3 and 3 warps on the four
+    // partitions, so the extra density work lands on the last two.  With a
+    // warp count that is a multiple of 4 the order is the identity.
+    const int tid_late = [&] {
+        constexpr int NW = T::NT / 32;
+        const int w = tid >> 5;
+        const int load_w = (NW - (w & 3) + 3) >> 2;
+        int idx = 0;
+#pragma unroll
+        for (int v = 0; v < NW; ++v) {
+            const int load_v = (NW - (v & 3) + 3) >> 2;
+            idx += (load_v < load_w || (load_v == load_w && v < w)) ? 1 : 0;
+        }
+        return idx * 32 + (tid & 31);
+    }();
 
     // ---- phase A, first part: raw plane q (tile + 2-cell halo) ----
     auto raw_entry = [&](int q, int e) -> RawCell {
@@ -117,7 +135,7 @@ __device__ __forceinline__ void fused_item(const DevParams &P, const Geo &G, con
         DenMeta *dm = dmeta + ring4(L) * T::DN;
         float *da = dat + ring4(L) * T::DN;
         const int gz = wrap_coord(L, G.nz, P.per[2]);
-        for (int e = tid; e < T::DN; e += T::NT) {
+        for (int e = tid, pass = 1; e < T::DN; e = pass++ * T::NT + tid_late) {
             const int dx = e % T::DX, dy = e / T::DX;
             const RawCell me = r1[(dx + 1) + T::RX * (dy + 1)];
             DenCell dc = {me.f0A, me.f0B, 0.f, 0.f, 0.f, 0.f};
