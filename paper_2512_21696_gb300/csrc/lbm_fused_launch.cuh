@@ -108,7 +108,8 @@ static cudaError_t launch_fused_tile(lbm_ctx *ctx, bool write_macro, LY ly)
 // resident CTA takes per plane, times the waves.  Per-plane times of the
 // three shapes on a GB300 (F32, 2070 MHz), fitted to the 128^3 drainage and
 // 192^3 fibre-bundle steps (32x8: 12.26 and 12.59 us measured; 64x8: 12.24 and
-// 12.19; 64x7: 11.8 and 11.7): 12.45, 12.2 and 11.8 us.  64x7 wins where its
+// 12.19; 64x7: 11.8 and 11.7, then 11.26 on 128^3 with the density pass's
+// sub-partition order): 12.45, 12.2 and 11.3 us.  64x7 wins where its
 // extra columns fill the SMs (128^3: 152 items on 152 slots, against 128 of
 // 152 for 64x8 and 256 of 304 for 32x8), 64x8 where both fill them (192^3);
 // lattices whose width is not a multiple of 64 keep 32x8.
@@ -122,7 +123,7 @@ static int auto_tile(lbm_ctx *ctx)
         int tile, tx, ty;
         double t_plane;
         int slots;
-    } cand[3] = {{2, 32, 8, 12.45, 0}, {4, 64, 8, 12.2, 0}, {7, 64, 7, 11.8, 0}};
+    } cand[3] = {{2, 32, 8, 12.45, 0}, {4, 64, 8, 12.2, 0}, {7, 64, 7, 11.3, 0}};
     if (fused_slots<32, 8, 2, false, false, LayF32>(ctx, &cand[0].slots) != cudaSuccess ||
         fused_slots<64, 8, 1, false, false, LayF32>(ctx, &cand[1].slots) != cudaSuccess ||
         fused_slots<64, 7, 1, false, false, LayF32>(ctx, &cand[2].slots) != cudaSuccess) {
