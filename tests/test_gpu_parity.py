@@ -451,7 +451,11 @@ def test_tile_choice_per_grid(shape, storage, want):
     its 38 columns x 4 chunks fill the 152 one-CTA slots (128^3), 64x8 where
     both 64-wide shapes fill them (192 x 192 planes), 32x8 on widths that are
     not a multiple of 64; the shifted 16-bit storage always runs 32x8."""
+    import torch
+
     from paper_2512_21696_gb300 import lbm
+    if torch.cuda.get_device_properties(0).multi_processor_count != 152:
+        pytest.skip("the expected shapes are those of a 152-SM GB300")
     nz, ny, nx = shape
     ctx = lbm.lbm_create(lbm.lbm_default_params(nx, ny, nz, storage=storage))
     try:
