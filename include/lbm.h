@@ -349,8 +349,8 @@ LBM_API int lbm_profile_read(lbm_ctx *ctx, lbm_kernel_stat *out, int max, int *c
  * 0 = 32x8 columns, 1 = 32x16, 2 = 32x8 with two CTAs per SM, 3 = 32x12,
  * 4 = 64x8, 7 = 64x7, 8 = chosen per grid among 2, 4 and 7 (the one whose
  * z-chunked columns best fill the resident CTA slots; 4 and 7 only where nx
- * is a multiple of 64; the shifted 16-bit storages run 2, the
- * rest-referenced ones 2, 4 or 7, tiles 0, 1, 3 there running 2), 5 and 6 = the
+ * is a multiple of 64; the shifted 16-bit storages run 2 or 7, the
+ * rest-referenced ones 2, 4 or 7, other tiles there running 2), 5 and 6 = the
  * published-density march on 32x8 and 32x7 tiles
  * (every CTA resident, one cooperative launch per step: each tile publishes
  * its densities and reads its ring from its neighbours instead of

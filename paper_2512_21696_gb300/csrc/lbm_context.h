@@ -93,7 +93,8 @@ cudaError_t launch_density(lbm_ctx *ctx);
 cudaError_t launch_collide(lbm_ctx *ctx, bool write_macro);
 cudaError_t launch_fused(lbm_ctx *ctx, bool write_macro);
 // The fused tile a step of ctx runs: the requested one, with tile 8 resolved
-// to its per-grid choice and the shapes a storage does not have mapped to 2.
+// to its per-grid choice and the shapes a storage does not have mapped to 2
+// (the shifted 16-bit kernel has 32x8 and 64x7).
 int fused_tile_in_use(lbm_ctx *ctx);
 // The published-density march (tiles 5 and 6); *ran false where it does not apply.
 cudaError_t launch_march(lbm_ctx *ctx, bool write_macro, bool *ran);

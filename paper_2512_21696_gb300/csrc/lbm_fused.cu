@@ -13,7 +13,7 @@ int fused_tile_in_use(lbm_ctx *ctx)
 {
     int tile = ctx->tile;
     if (tile == 8) tile = auto_tile<>(ctx);
-    if (ctx->p.storage == LBM_STORAGE_F16S || ctx->p.storage == LBM_STORAGE_BF16S) return 2;
+    if (ctx->p.storage == LBM_STORAGE_F16S || ctx->p.storage == LBM_STORAGE_BF16S) return tile == 7 ? 7 : 2;
     if ((ctx->p.storage == LBM_STORAGE_F16R || ctx->p.storage == LBM_STORAGE_BF16R) && tile != 4 && tile != 7)
         return 2;
     return tile;

@@ -52,6 +52,21 @@ __global__ void __launch_bounds__(TX *TY, MINB)
 
     const int n = P.n;
     const int tid = threadIdx.x;
+    // the den region's entries beyond the first pass go first to the warps of
+    // the SM sub-partitions holding fewer collision warps (warp w runs on
+    // partition w % 4; the identity for warp counts that are multiples of 4)
+    const int tid_late = [&] {
+        constexpr int NW = T::NT / 32;
+        const int w = tid >> 5;
+        const int load_w = (NW - (w & 3) + 3) >> 2;
+        int idx = 0;
+#pragma unroll
+        for (int v = 0; v < NW; ++v) {
+            const int load_v = (NW - (v & 3) + 3) >> 2;
+            idx += (load_v < load_w || (load_v == load_w && v < w)) ? 1 : 0;
+        }
+        return idx * 32 + (tid & 31);
+    }();
     const int tiles_x = (P.nx + TX - 1) / TX, tiles_y = (P.ny + TY - 1) / TY;
     const int ncol = tiles_x * tiles_y;
 
@@ -67,7 +82,7 @@ __global__ void __launch_bounds__(TX *TY, MINB)
             DenLP *dd = den + ring4_lp(L) * T::DN;
             int *dg = dgi + ring4_lp(L) * T::DN;
             const int gz = wrap_lp(L, P.nz, P.per[2]);
-            for (int e = tid; e < T::DN; e += T::NT) {
+            for (int e = tid, pass = 1; e < T::DN; e = pass++ * T::NT + tid_late) {
                 const int gx = wrap_lp(x0 - 1 + e % T::DX, P.nx, P.per[0]);
                 const int gy = wrap_lp(y0 - 1 + e / T::DX, P.ny, P.per[1]);
                 DenLP dc = {0.f, 0.f, P.at_wall, CELL_SOLID};
@@ -217,6 +232,8 @@ static cudaError_t launch_lp_t(lbm_ctx *ctx)
 template <class H>
 static cudaError_t launch_lp_h(lbm_ctx *ctx, bool write_macro)
 {
+    if (fused_tile_in_use(ctx) == 7)  // the grids where 64x7 fills the SMs
+        return write_macro ? launch_lp_t<64, 7, 1, true, H>(ctx) : launch_lp_t<64, 7, 1, false, H>(ctx);
     return write_macro ? launch_lp_t<32, 8, 2, true, H>(ctx) : launch_lp_t<32, 8, 2, false, H>(ctx);
 }
 

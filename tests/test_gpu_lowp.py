@@ -109,12 +109,12 @@ def test_lowp_checkpoint_roundtrip(storage, cell_bytes):
         ctx.close()
 
 
-@pytest.mark.parametrize("storage", [3, 4])
+@pytest.mark.parametrize("storage", [1, 2, 3, 4])
 @pytest.mark.parametrize("tile", [4, 7, 8])
 @pytest.mark.parametrize("n,steps", [(48, 20), (128, 3)])
-def test_rest_referenced_tile_shapes_are_bit_identical(storage, tile, n, steps):
-    """F16R / BF16R on the 64-wide tiles and the automatic choice compute the
-    32x8 tile's states bit for bit (fields and observables)."""
+def test_16bit_tile_shapes_are_bit_identical(storage, tile, n, steps):
+    """The 16-bit storages on the 64-wide tiles and the automatic choice
+    compute the 32x8 tile's states bit for bit (fields and observables)."""
     case = LC.drainage(n)
     a, ga, _ = LC.run_gpu(case, steps, storage=storage, tile=tile)
     b, gb, _ = LC.run_gpu(case, steps, storage=storage, tile=2)

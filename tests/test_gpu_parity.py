@@ -445,12 +445,13 @@ def test_fibre_bundle_tensorial_400_steps(axis):
 
 
 @pytest.mark.parametrize("shape,storage,want", [((128, 128, 128), 0, 7), ((8, 192, 192), 0, 4), ((96, 96, 96), 0, 2),
-                                                ((24, 24, 24), 0, 2), ((128, 128, 128), 3, 7), ((128, 128, 128), 1, 2)])
+                                                ((24, 24, 24), 0, 2), ((128, 128, 128), 3, 7), ((128, 128, 128), 1, 7),
+                                                ((8, 192, 192), 1, 2)])
 def test_tile_choice_per_grid(shape, storage, want):
     """The default tile (8) resolves per grid on the 152-SM GB300: 64x7 where
     its 38 columns x 4 chunks fill the 152 one-CTA slots (128^3), 64x8 where
     both 64-wide shapes fill them (192 x 192 planes), 32x8 on widths that are
-    not a multiple of 64; the shifted 16-bit storage always runs 32x8."""
+    not a multiple of 64; the shifted 16-bit kernel has 32x8 and 64x7 only."""
     import torch
 
     from paper_2512_21696_gb300 import lbm
@@ -462,6 +463,8 @@ def test_tile_choice_per_grid(shape, storage, want):
         assert lbm.lbm_get_kernel(ctx) == (0, want)
         lbm.lbm_set_kernel(ctx, 0, 3)
         assert lbm.lbm_get_kernel(ctx) == (0, 3 if storage == 0 else 2)
+        lbm.lbm_set_kernel(ctx, 0, 4)
+        assert lbm.lbm_get_kernel(ctx) == (0, 2 if storage == 1 else 4)
         lbm.lbm_set_kernel(ctx, 1, 5)
         assert lbm.lbm_get_kernel(ctx) == (1, 5)
     finally:
